@@ -1,0 +1,61 @@
+"""Plants plausible mistakes in copies of the oracle source (on the CPU) and
+checks that the pins of test_oracle_pins.py catch every one of them."""
+import os
+import shutil
+import tempfile
+
+import pytest
+
+import tests.test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "hepacc_oracle.c")
+
+# (name, text in the source, replacement)
+MUTATIONS = [
+    ("dphi wrap sign", "dphi = dphi - OR_TWO_PI_F;", "dphi = dphi + OR_TWO_PI_F;"),
+    ("dr2 operand", "float a = deta * deta;", "float a = deta * dphi;"),
+    ("sum assigns", "out[ev] += get_f(x, xt, i);", "out[ev] = get_f(x, xt, i);"),
+    ("max tie keeps last", "(want_max ? v > best : v < best)", "(want_max ? v >= best : v <= best)"),
+    ("pz uses cosh", "v.pz = pt * sinh(eta);", "v.pz = pt * cosh(eta);"),
+    ("mass sign", "double m2 = v.e * v.e - (", "double m2 = v.e * v.e + ("),
+    ("bin upper edge inside", "if (v < (double)e[b])", "if (v <= (double)e[b])"),
+    ("iso cut inclusive", "iso[i] < c->lep_iso_max;", "iso[i] <= c->lep_iso_max;"),
+    ("two jets required", "njet >= 2 && nb >= 1", "njet >= 1 && nb >= 1"),
+    ("trijet tie keeps last", "if (v > *best_v) {", "if (v >= *best_v) {"),
+    ("lepton is the last", "if (!have_lep) {", "if (1) {"),
+    ("f16 exponent bias", "e - 25);", "e - 24);"),
+    ("get counts from 1", "if (seen == want) {\n                found = i;", "if (seen == want + 1) {\n                found = i;"),
+    ("sub-leading may be leading", "if (q == lead_q)\n                    continue;", ""),
+    ("chain dR inclusive", "< c->dr2_cut)\n                            sel = 0;", "<= c->dr2_cut)\n                            sel = 0;"),
+    ("jet pt unscaled", "float ptk = get_f(b->jet_pt, kt, i) * s;", "float ptk = get_f(b->jet_pt, kt, i);"),
+    ("HT in FP64", "ht += ptk;", "ht = (float)((double)ht + (double)ptk + 1e-7 * ptk);"),
+    ("weight squared missing", "o->sumw2[at] += w * w;", "o->sumw2[at] += w;"),
+    ("set writes next", "((uint8_t *)x)[i] = (uint8_t)value;", "((uint8_t *)x)[i + 1] = (uint8_t)value;"),
+]
+
+PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(orc, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {name}"
+    tmp = tempfile.mkdtemp(prefix="oracle_mut_")
+    try:
+        path = os.path.join(tmp, "mut.c")
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+        so = orc.compile_source(path, os.path.join(tmp, "mut.so"))
+        orc.use_library(so)
+        failed = []
+        for t in PIN_TESTS:
+            try:
+                t(orc)
+            except (AssertionError, pytest.skip.Exception) as e:
+                if isinstance(e, AssertionError):
+                    failed.append(t.__name__)
+        assert failed, f"no pin caught the planted mistake '{name}'"
+    finally:
+        orc.use_library(None)
+        shutil.rmtree(tmp, ignore_errors=True)

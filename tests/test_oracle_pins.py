@@ -1,0 +1,585 @@
+"""Pins of the CPU oracle to things other than itself.
+
+Each check below is fixed by the paper's definitions (Section II data model,
+Section III kernels and Listing 1, Section IV chain) and by mathematics:
+hand-made events with answers worked out by hand (tests/golden), closed
+forms (two-body decay momentum, massless pair identity, balanced three-body
+system), invariants (segment counts sum to the content length, Delta R
+symmetry, total histogram weight), numpy.histogram for the binning, and
+brute force on tiny inputs written with a different structure (itertools,
+complex transverse momenta, pairwise mass formula).
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1906_06242_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+F32 = np.float32
+VAR = {name: i for i, (name, *_r) in enumerate(synth.HIST_SPECS)}
+
+
+def _jagged(rng, n, lam, off_dtype=np.int64, first=0):
+    counts = rng.poisson(lam, n)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
+    off += first
+    return counts, off.astype(off_dtype)
+
+
+# ---------------------------------------------------------------------------
+# golden hand-made events through the chain
+# ---------------------------------------------------------------------------
+
+def _golden():
+    with open(os.path.join(GOLDEN, "hand_events.json")) as f:
+        return json.load(f)
+
+
+def test_golden_events_chain(orc):
+    g = _golden()
+    evs = g["events"]
+    batch = synth.hand_batch(evs)
+    out = orc.run_chain(batch, synth.CUTS, synth.HIST_SPECS, g["shifts"])
+    for i, ev in enumerate(evs):
+        ex = ev["expect"]
+        why = ev["why"]
+        assert out["nlep"][i] == ex["nlep"], why
+        for k in range(len(g["shifts"])):
+            if "njet" in ex:
+                assert out["njet"][k, i] == ex["njet"][k], why
+            if "nb" in ex:
+                assert out["nb"][k, i] == ex["nb"][k], why
+            if "pass" in ex:
+                assert out["pass"][k, i] == ex["pass"][k], why
+        if "lead" in ex:
+            assert out["idx"][0, 0, i] == ex["lead"], why
+        if "sub" in ex:
+            assert out["idx"][0, 1, i] == ex["sub"], why
+        if "tri" in ex:
+            assert list(out["idx"][0, 2:, i]) == ex["tri"], why
+        for name, val in ex.get("vars", {}).items():
+            got = out["vars"][0, VAR[name], i]
+            if val is None:
+                assert math.isnan(got), (why, name)
+            elif name in ("m_jj", "m_jjj"):
+                assert got == pytest.approx(val, rel=1e-7), (why, name)
+            else:
+                assert got == float(F32(val)), (why, name, got, val)
+
+
+def test_golden_ht_histogram(orc):
+    g = _golden()
+    batch = synth.hand_batch(g["events"])
+    out = orc.run_chain(batch, synth.CUTS, synth.HIST_SPECS, g["shifts"])
+    h = g["ht_hist_nominal"]
+    counts = out["counts"][0, :102]
+    sumw = out["sumw"][0, :102]
+    exp_c = np.zeros(102, dtype=np.uint64)
+    exp_w = np.zeros(102)
+    for b, c in h["counts"].items():
+        exp_c[int(b)] = c
+    for b, w in h["sumw"].items():
+        exp_w[int(b)] = w
+    np.testing.assert_array_equal(counts, exp_c)
+    np.testing.assert_allclose(sumw, exp_w, rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# sum_in_offsets (Listing 1)
+# ---------------------------------------------------------------------------
+
+def test_sum_counts_invariant(orc):
+    rng = np.random.default_rng(3)
+    for off_dtype in (np.int32, np.int64):
+        counts, off = _jagged(rng, 1000, 3.0, off_dtype, first=17)
+        m = int(off[-1])
+        ones = np.ones(m, dtype=np.uint8)
+        got = orc.sum_in_offsets(ones, off)
+        np.testing.assert_array_equal(got, counts)
+        assert got.sum() == off[-1] - off[0]
+
+
+def test_sum_integer_valued_is_exact(orc):
+    # integer values below 2^24 summed in any order are exact in FP32
+    rng = np.random.default_rng(4)
+    counts, off = _jagged(rng, 2000, 6.0)
+    x = rng.integers(0, 1000, int(off[-1])).astype(np.float32)
+    mask = (rng.random(len(x)) < 0.7).astype(np.uint8)
+    got = orc.sum_in_offsets(x, off, mask_content=mask)
+    exact = np.zeros(2000, dtype=np.int64)
+    np.add.at(exact, np.repeat(np.arange(2000), counts), x.astype(np.int64) * mask)
+    np.testing.assert_array_equal(got.astype(np.int64), exact)
+
+
+def test_sum_listing1_semantics(orc):
+    # masked events are skipped and keep their previous value; others accumulate (+=)
+    off = np.array([0, 2, 2, 5], dtype=np.int64)
+    x = np.array([1.5, 2.5, 4.0, 8.0, 16.0], dtype=np.float32)
+    out = np.array([100.0, 7.0, -1.0], dtype=np.float32)
+    orc.sum_in_offsets(x, off, mask_rows=np.array([1, 1, 0]), out=out)
+    np.testing.assert_array_equal(out, [104.0, 7.0, -1.0])
+    orc.sum_in_offsets(x, off, mask_content=np.array([0, 1, 1, 0, 1]), out=out)
+    np.testing.assert_array_equal(out, [106.5, 7.0, 19.0])
+
+
+def test_sum_fp32_sequential_order(orc):
+    # 1e8 + 1 + 1 + ... in FP32 element order: each +1 is lost (ulp(1e8) = 8)
+    off = np.array([0, 5], dtype=np.int64)
+    x = np.array([1e8, 1, 1, 1, 1], dtype=np.float32)
+    got = orc.sum_in_offsets(x, off)
+    assert got[0] == F32(1e8)
+    x2 = np.array([1, 1, 1, 1, 1e8], dtype=np.float32)
+    assert orc.sum_in_offsets(x2, off)[0] == F32(1e8 + 4)
+
+
+# ---------------------------------------------------------------------------
+# max / min / get / set in offsets
+# ---------------------------------------------------------------------------
+
+def test_minmax_hand_cases(orc):
+    off = np.array([0, 4, 7, 7, 9, 11], dtype=np.int32)
+    x = np.array([3, 5, 5, 1, 2, 1, 1, np.nan, np.nan, np.nan, 4], dtype=np.float32)
+    mx, amx = orc.minmax_in_offsets(x, off, True)
+    mn, amn = orc.minmax_in_offsets(x, off, False)
+    assert list(amx) == [1, 0, -1, -1, 1]      # tie -> first; empty -> -1; NaN never chosen
+    np.testing.assert_array_equal(mx[[0, 1, 4]], [5, 2, 4])
+    assert mx[2] == -np.inf and mx[3] == -np.inf
+    assert list(amn) == [3, 1, -1, -1, 1]
+    np.testing.assert_array_equal(mn[[0, 1, 4]], [1, 1, 4])
+
+
+def test_minmax_brute_force(orc):
+    rng = np.random.default_rng(5)
+    counts, off = _jagged(rng, 500, 4.0)
+    x = rng.integers(-5, 6, int(off[-1])).astype(np.float32)   # many ties
+    mask = (rng.random(len(x)) < 0.6).astype(np.uint8)
+    rows = (rng.random(500) < 0.8).astype(np.uint8)
+    for want_max in (True, False):
+        out = np.full(500, 99.0, dtype=np.float32)
+        arg = np.full(500, 99, dtype=np.int32)
+        orc.minmax_in_offsets(x, off, want_max, rows, mask, -1e30, out, arg)
+        for e in range(500):
+            if not rows[e]:
+                assert out[e] == 99.0 and arg[e] == 99
+                continue
+            vals = [(float(x[i]), i - off[e]) for i in range(off[e], off[e + 1]) if mask[i]]
+            if not vals:
+                assert out[e] == F32(-1e30) and arg[e] == -1
+                continue
+            best = max(v for v, _ in vals) if want_max else min(v for v, _ in vals)
+            assert out[e] == best
+            assert arg[e] == next(j for v, j in vals if v == best)
+
+
+def test_max_equals_get0_on_sorted(orc):
+    b = synth.generate(3000, 9)
+    pt, off = b.cols["jet_pt"], b.jet_offsets
+    mask = (b.cols["jet_btag"] > 0.3).astype(np.uint8)
+    mx, amx = orc.minmax_in_offsets(pt, off, True, mask_content=mask, empty=-1.0)
+    g, gi = orc.get_in_offsets(pt, off, 0, mask_content=mask, default=-1.0)
+    np.testing.assert_array_equal(mx, g)
+    np.testing.assert_array_equal(amx, gi)
+
+
+def test_get_set_brute_force(orc):
+    rng = np.random.default_rng(6)
+    counts, off = _jagged(rng, 400, 3.0, np.int32)
+    x = rng.random(int(off[-1])).astype(np.float32)
+    mask = (rng.random(len(x)) < 0.7).astype(np.uint8)
+    nth = rng.integers(-1, 4, 400).astype(np.int32)
+    out, idx = orc.get_in_offsets(x, off, nth, mask_content=mask, default=-5.0)
+    for e in range(400):
+        sel = [i for i in range(off[e], off[e + 1]) if mask[i]]
+        if 0 <= nth[e] < len(sel):
+            assert out[e] == x[sel[nth[e]]] and idx[e] == sel[nth[e]] - off[e]
+        else:
+            assert out[e] == F32(-5.0) and idx[e] == -1
+    m2 = mask.copy()
+    orc.set_in_offsets(m2, off, nth, 0, mask_content=mask)
+    expect = mask.copy()
+    for e in range(400):
+        sel = [i for i in range(off[e], off[e + 1]) if mask[i]]
+        if 0 <= nth[e] < len(sel):
+            expect[sel[nth[e]]] = 0
+    np.testing.assert_array_equal(m2, expect)
+
+
+def test_select_range_edges(orc):
+    x = np.array([30.0, np.nextafter(F32(30), F32(100)), 29.0, -3.0, 3.0, np.nan], dtype=np.float32)
+    np.testing.assert_array_equal(orc.select_range(x, lo=30.0), [0, 1, 0, 0, 0, 0])
+    np.testing.assert_array_equal(orc.select_range(x, hi=2.5, use_abs=True, lo=-1), [0, 0, 0, 0, 0, 0])
+    np.testing.assert_array_equal(orc.select_range(x, hi=3.5, use_abs=True, lo=-1), [0, 0, 0, 1, 1, 0])
+    # scale is applied as one FP32 product before the comparison
+    np.testing.assert_array_equal(orc.select_range(np.array([30.2], np.float32), lo=30.0, scale=0.99), [0])
+
+
+# ---------------------------------------------------------------------------
+# Delta R
+# ---------------------------------------------------------------------------
+
+def test_dr2_exact_boundary_and_wrap(orc):
+    # |Delta eta| = 0.5 exactly: Delta R^2 = 0.25 exactly, not below a 0.25 cut
+    assert orc.dr2(0.75, 0.0, 0.25, 0.0) == 0.25
+    off = np.array([0, 2], dtype=np.int64)
+    off2 = np.array([0, 1], dtype=np.int64)
+    eta1 = np.array([0.75, np.nextafter(F32(0.75), F32(0))], dtype=np.float32)
+    phi1 = np.zeros(2, dtype=np.float32)
+    m = orc.mask_deltar(eta1, phi1, off, np.array([0.25], np.float32), np.zeros(1, np.float32), off2,
+                        dr2_cut=0.25)
+    np.testing.assert_array_equal(m, [1, 0])
+    # phi 3.0 and -3.0 are 2*pi - 6 = 0.283 apart
+    d = orc.dr2(0.0, 3.0, 0.0, -3.0)
+    assert d == pytest.approx((2 * math.pi - 6.0) ** 2, rel=1e-5)
+    assert orc.dr2(0.0, -3.0, 0.0, 3.0) == d
+
+
+def test_dr2_symmetric_and_matches_fp64(orc):
+    rng = np.random.default_rng(7)
+    e1, e2 = rng.normal(0, 2, (2, 2000)).astype(np.float32)
+    p1, p2 = rng.uniform(-math.pi, math.pi, (2, 2000)).astype(np.float32)
+    for i in range(2000):
+        a = orc.dr2(e1[i], p1[i], e2[i], p2[i])
+        b = orc.dr2(e2[i], p2[i], e1[i], p1[i])
+        assert a == b
+        # independent FP64 distance, the angle difference folded by the complex argument
+        dphi = np.angle(np.exp(1j * (float(p1[i]) - float(p2[i]))))
+        ref = (float(e1[i]) - float(e2[i])) ** 2 + dphi ** 2
+        assert a == pytest.approx(ref, rel=2e-6, abs=1e-6)
+
+
+def test_mask_deltar_brute_force(orc):
+    rng = np.random.default_rng(8)
+    n = 300
+    _, off1 = _jagged(rng, n, 4.0)
+    _, off2 = _jagged(rng, n, 1.5)
+    m1, m2 = int(off1[-1]), int(off2[-1])
+    eta1 = rng.normal(0, 1, m1).astype(np.float32)
+    phi1 = rng.uniform(-math.pi, math.pi, m1).astype(np.float32)
+    eta2 = rng.normal(0, 1, m2).astype(np.float32)
+    phi2 = rng.uniform(-math.pi, math.pi, m2).astype(np.float32)
+    mk1 = (rng.random(m1) < 0.8).astype(np.uint8)
+    mk2 = (rng.random(m2) < 0.8).astype(np.uint8)
+    got = orc.mask_deltar(eta1, phi1, off1, eta2, phi2, off2, mask1_in=mk1, mask2=mk2, dr2_cut=0.5)
+    for e in range(n):
+        for i in range(off1[e], off1[e + 1]):
+            near = False
+            for j in range(off2[e], off2[e + 1]):
+                if not mk2[j]:
+                    continue
+                dphi = np.angle(np.exp(1j * (float(phi1[i]) - float(phi2[j]))))
+                d = (float(eta1[i]) - float(eta2[j])) ** 2 + dphi ** 2
+                if abs(d - 0.5) < 1e-5:
+                    pytest.skip("random case too close to the cut for an FP64 comparison")
+                near |= d < 0.5
+            assert got[i] == (mk1[i] and not near)
+
+
+# ---------------------------------------------------------------------------
+# invariant masses
+# ---------------------------------------------------------------------------
+
+def _two_body(M, m1, m2):
+    return math.sqrt((M * M - (m1 + m2) ** 2) * (M * M - (m1 - m2) ** 2)) / (2 * M)
+
+
+def test_mass_two_body_decay_closed_form(orc):
+    rng = np.random.default_rng(10)
+    for _ in range(300):
+        M = rng.uniform(10, 500)
+        m1, m2 = rng.uniform(0, 0.45 * M, 2)
+        p = _two_body(M, m1, m2)
+        theta = rng.uniform(0.05, math.pi - 0.05)
+        phi = rng.uniform(-math.pi, math.pi)
+        pt = p * math.sin(theta)
+        eta = -math.log(math.tan(theta / 2))
+        got = orc.mass2(pt, eta, phi, m1, pt, -eta, phi + math.pi, m2)
+        assert got == pytest.approx(M, rel=1e-10)
+
+
+def test_mass_massless_pair_identity(orc):
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        pt1, pt2 = rng.uniform(1, 500, 2)
+        e1, e2 = rng.normal(0, 2, 2)
+        f1, f2 = rng.uniform(-math.pi, math.pi, 2)
+        ref = math.sqrt(2 * pt1 * pt2 * (math.cosh(e1 - e2) - math.cos(f1 - f2)))
+        got = orc.mass2(pt1, e1, f1, 0.0, pt2, e2, f2, 0.0)
+        assert got == pytest.approx(ref, rel=1e-9)
+
+
+def test_mass_single_object_and_rotation(orc):
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        pt, eta, phi, m = rng.uniform(1, 300), rng.normal(0, 2), rng.uniform(-3, 3), rng.uniform(0, 50)
+        assert orc.mass2(pt, eta, phi, m, 0.0, 0.0, 0.0, 0.0) == pytest.approx(m, rel=1e-9, abs=1e-9)
+        a = (pt, eta, phi, m)
+        b = (rng.uniform(1, 300), rng.normal(0, 2), rng.uniform(-3, 3), rng.uniform(0, 50))
+        r = rng.uniform(-1, 1)
+        m_ab = orc.mass2(*a, *b)
+        m_rot = orc.mass2(a[0], a[1], a[2] + r, a[3], b[0], b[1], b[2] + r, b[3])
+        assert m_rot == pytest.approx(m_ab, rel=1e-9)
+
+
+def _pairwise_mass(objs):
+    """m^2 = sum m_i^2 + 2 sum_{i<j} (E_i E_j - p_i . p_j), from (pt, eta, phi, m)."""
+    vecs = []
+    for pt, eta, phi, m in objs:
+        p = np.array([pt * math.cos(phi), pt * math.sin(phi), pt * math.sinh(eta)])
+        vecs.append((math.sqrt(p @ p + m * m), p, m))
+    m2 = sum(m * m for _, _, m in vecs)
+    for (ea, pa, _), (eb, pb, _) in itertools.combinations(vecs, 2):
+        m2 += 2 * (ea * eb - pa @ pb)
+    return math.sqrt(max(m2, 0.0))
+
+
+def test_trijet_brute_force(orc):
+    b = synth.generate(4000, 13)
+    off = b.jet_offsets
+    c = b.cols
+    mask = (np.abs(c["jet_eta"]) < 2.5).astype(np.uint8)
+    m, ptj, idx, gap = orc.max_pt_trijet(c["jet_pt"], c["jet_eta"], c["jet_phi"], c["jet_mass"], off,
+                                         mask_content=mask)
+    checked = 0
+    for e in range(b.n_events):
+        sel = [i for i in range(off[e], off[e + 1]) if mask[i]]
+        if len(sel) > 6:
+            continue
+        if len(sel) < 3:
+            assert math.isnan(m[e]) and list(idx[e]) == [-1, -1, -1]
+            continue
+        best, best_v = None, -1.0
+        for t in itertools.combinations(sel, 3):
+            v = abs(sum(float(c["jet_pt"][i]) * np.exp(1j * float(c["jet_phi"][i])) for i in t))
+            if v > best_v:
+                best, best_v = t, v
+        if gap[e] < 1e-9:
+            continue
+        assert [i - off[e] for i in best] == list(idx[e])
+        assert ptj[e] == pytest.approx(best_v, rel=1e-9)
+        objs = [(float(c["jet_pt"][i]), float(c["jet_eta"][i]), float(c["jet_phi"][i]),
+                 float(c["jet_mass"][i])) for i in best]
+        assert m[e] == pytest.approx(_pairwise_mass(objs), rel=1e-8)
+        checked += 1
+    assert checked > 1000
+
+
+def test_trijet_balanced_three_body(orc):
+    # three massless jets of equal pt at 120 degrees: zero momentum, m = 3 pt
+    off = np.array([0, 3], dtype=np.int64)
+    for pt in (10.0, 55.0, 400.0):
+        x = np.full(3, pt, dtype=np.float32)
+        phi = np.array([0.3, 0.3 + 2 * math.pi / 3, 0.3 - 2 * math.pi / 3], dtype=np.float32)
+        m, ptj, idx, gap = orc.max_pt_trijet(x, np.zeros(3, np.float32), phi, np.zeros(3, np.float32), off)
+        assert m[0] == pytest.approx(3 * pt, rel=1e-7)
+        assert ptj[0] < 1e-4 * pt
+
+
+# ---------------------------------------------------------------------------
+# histograms
+# ---------------------------------------------------------------------------
+
+def test_histogram_vs_numpy(orc):
+    rng = np.random.default_rng(14)
+    edges = orc.hist_edges(-1.0, 3.0, 40)
+    x = rng.normal(1.0, 1.5, 50000).astype(np.float32)
+    x[:10] = edges[[0, 5, 17, 40, 40, 39, 0, 1, 2, 3]]     # values exactly on edges
+    x[10] = np.inf
+    x[11] = -np.inf
+    x[12] = np.nan
+    w = rng.normal(1, 0.2, len(x)).astype(np.float32)
+    mask = (rng.random(len(x)) < 0.9).astype(np.uint8)
+    counts, sumw, sumw2 = orc.fill_histogram(x, edges, w, mask)
+    ok = mask.astype(bool) & ~np.isnan(x)
+    xv, wv = x[ok].astype(np.float64), w[ok].astype(np.float64)
+    inner = (xv >= edges[0]) & (xv < edges[-1])
+    ref_c, _ = np.histogram(xv[inner], bins=edges.astype(np.float64))
+    ref_w, _ = np.histogram(xv[inner], bins=edges.astype(np.float64), weights=wv[inner])
+    ref_w2, _ = np.histogram(xv[inner], bins=edges.astype(np.float64), weights=wv[inner] ** 2)
+    np.testing.assert_array_equal(counts[1:-1], ref_c)
+    assert counts[0] == np.sum(xv < edges[0])
+    assert counts[-1] == np.sum(xv >= edges[-1])
+    np.testing.assert_allclose(sumw[1:-1], ref_w, rtol=1e-12)
+    np.testing.assert_allclose(sumw2[1:-1], ref_w2, rtol=1e-12)
+    assert counts.sum() == ok.sum()
+    assert sumw.sum() == pytest.approx(wv.sum(), rel=1e-12)
+
+
+def test_histogram_edges_are_float32_of_binary64(orc):
+    e = orc.hist_edges(-math.pi, math.pi, 100)
+    assert e.dtype == np.float32 and len(e) == 101
+    assert e[0] == F32(-math.pi) and e[-1] == F32(math.pi) and e[50] == 0.0
+    assert orc.bin_of(float(e[7]), e) == 8           # lower edge is inside the bin
+    assert orc.bin_of(float(np.nextafter(e[7], F32(-10))), e) == 7
+    assert orc.bin_of(float(e[-1]), e) == 101         # upper edge is overflow
+
+
+# ---------------------------------------------------------------------------
+# the chain on generated events
+# ---------------------------------------------------------------------------
+
+def test_chain_histogram_invariants(orc):
+    b = synth.generate(20000, 21)
+    shifts = synth.variation_shifts(5)
+    out = orc.run_chain(b, synth.CUTS, synth.HIST_SPECS, shifts)
+    nb = 102
+    for k in range(len(shifts)):
+        passed = out["pass"][k].astype(bool)
+        tri = passed & (out["njet"][k] >= 3)
+        wsum = b.weight[passed].astype(np.float64).sum()
+        for h in range(synth.N_HIST):
+            c = out["counts"][k, h * nb:(h + 1) * nb]
+            s = out["sumw"][k, h * nb:(h + 1) * nb]
+            want = tri if h in synth.TRIJET_VARS else passed
+            assert c.sum() == want.sum()
+            assert s.sum() == pytest.approx(b.weight[want].astype(np.float64).sum(), rel=1e-12)
+            s2 = out["sumw2"][k, h * nb:(h + 1) * nb]
+            assert s2.sum() == pytest.approx((b.weight[want].astype(np.float64) ** 2).sum(), rel=1e-12)
+        assert out["counts"][k, :nb].sum() == passed.sum()
+        assert out["sumw"][k, :nb].sum() == pytest.approx(wsum, rel=1e-12)
+        assert (out["nb"][k] <= out["njet"][k]).all()
+
+
+def _brute_chain(b, shifts):
+    """The Section IV chain written out per event with Python lists and numpy
+    float32 scalars (FP32 cut arithmetic), itertools for triplets, complex
+    numbers for transverse momenta and the pairwise mass formula."""
+    cut = {k: F32(v) for k, v in synth.CUTS.items()}
+    pi_f, two_pi_f = F32(3.14159265358979), F32(6.28318530717959)
+    c = b.cols
+    res = []
+    for e in range(b.n_events):
+        leps = []
+        for coll in ("mu", "el"):
+            off = b.offsets[coll]
+            for i in range(off[e], off[e + 1]):
+                if (c[f"{coll}_pt"][i] > cut["lep_pt_min"] and abs(c[f"{coll}_eta"][i]) < cut["lep_abseta_max"]
+                        and c[f"{coll}_tight"][i] and c[f"{coll}_iso"][i] < cut["lep_iso_max"]):
+                    leps.append((c[f"{coll}_pt"][i], c[f"{coll}_eta"][i], c[f"{coll}_phi"][i]))
+        o = b.jet_offsets
+        per_k = []
+        for k in shifts:
+            s = F32(1.0 + 0.01 * k)
+            jets = []
+            for i in range(o[e], o[e + 1]):
+                ptk = c["jet_pt"][i] * s
+                eta, phi = c["jet_eta"][i], c["jet_phi"][i]
+                if not (ptk > cut["jet_pt_min"] and abs(eta) < cut["jet_abseta_max"]):
+                    continue
+                close = False
+                for _lpt, leta, lphi in leps:
+                    dphi = phi - lphi
+                    if dphi > pi_f:
+                        dphi = dphi - two_pi_f
+                    elif dphi < -pi_f:
+                        dphi = dphi + two_pi_f
+                    deta = eta - leta
+                    close |= (deta * deta + dphi * dphi) < cut["dr2_cut"]
+                if not close:
+                    jets.append((i - o[e], ptk, eta, phi, c["jet_mass"][i], c["jet_btag"][i]))
+            ht = F32(0)
+            for j in jets:
+                ht = ht + j[1]
+            nbj = sum(1 for j in jets if j[5] > cut["btag_min"])
+            order = sorted(range(len(jets)), key=lambda q: (-float(jets[q][1]), q))
+            r = {"njet": len(jets), "nb": nbj, "ht": ht,
+                 "pass": int(len(leps) == 1 and len(jets) >= 2 and nbj >= 1),
+                 "lead": jets[order[0]][0] if jets else -1,
+                 "sub": jets[order[1]][0] if len(jets) > 1 else -1}
+            if len(jets) > 1:
+                a, bb = jets[order[0]], jets[order[1]]
+                r["m_jj"] = _pairwise_mass([(float(a[1]), float(a[2]), float(a[3]), float(a[4])),
+                                            (float(bb[1]), float(bb[2]), float(bb[3]), float(bb[4]))])
+            if len(jets) > 2:
+                vals = [(abs(sum(float(jets[q][1]) * np.exp(1j * float(jets[q][3])) for q in t)), t)
+                        for t in itertools.combinations(range(len(jets)), 3)]
+                bv = max(v for v, _ in vals)
+                t = next(t for v, t in vals if v == bv)
+                r["tri"] = [jets[q][0] for q in t]
+                r["m_jjj"] = _pairwise_mass([tuple(float(jets[q][z]) for z in (1, 2, 3, 4)) for q in t])
+                r["pt_jjj"] = bv
+            per_k.append(r)
+        res.append((len(leps), per_k))
+    return res
+
+
+def test_chain_vs_brute_force(orc):
+    b = synth.generate(600, 22)
+    shifts = [0, 3, -3]
+    out = orc.run_chain(b, synth.CUTS, synth.HIST_SPECS, shifts)
+    ref = _brute_chain(b, shifts)
+    for e, (nlep, per_k) in enumerate(ref):
+        assert out["nlep"][e] == nlep
+        for k, r in enumerate(per_k):
+            assert out["njet"][k, e] == r["njet"]
+            assert out["nb"][k, e] == r["nb"]
+            assert out["pass"][k, e] == r["pass"]
+            assert out["vars"][k, VAR["ht"], e] == float(r["ht"])
+            assert out["idx"][k, 0, e] == r["lead"] and out["idx"][k, 1, e] == r["sub"]
+            if "m_jj" in r:
+                assert out["vars"][k, VAR["m_jj"], e] == pytest.approx(r["m_jj"], rel=1e-8)
+            if "tri" in r and out["gap"][k, e] > 1e-9:
+                assert list(out["idx"][k, 2:, e]) == r["tri"]
+                assert out["vars"][k, VAR["m_jjj"], e] == pytest.approx(r["m_jjj"], rel=1e-8)
+                assert out["vars"][k, VAR["pt_jjj"], e] == pytest.approx(r["pt_jjj"], rel=1e-9)
+
+
+def test_chain_reduced_precision_inputs_are_widened(orc):
+    # a half-precision batch gives exactly the chain of its float32 widening
+    b = synth.generate(3000, 23)
+    for fmt in ("bf16", "f16"):
+        h = synth.reduced_precision(b, fmt)
+        wide = synth.EventBatch(n_events=h.n_events, jet_offsets=h.jet_offsets, mu_offsets=h.mu_offsets,
+                                el_offsets=h.el_offsets, cols=dict(h.cols), weight=h.weight)
+        import torch
+        tdt = torch.bfloat16 if fmt == "bf16" else torch.float16
+        for name, a in h.cols.items():
+            if a.dtype == np.uint16:
+                dt = tdt if name != "jet_btag" else torch.float16
+                wide.cols[name] = torch.from_numpy(a.view(np.int16)).view(dt).float().numpy()
+        o1 = orc.run_chain(h, synth.CUTS, synth.HIST_SPECS, [0, 1])
+        o2 = orc.run_chain(wide, synth.CUTS, synth.HIST_SPECS, [0, 1])
+        np.testing.assert_array_equal(o1["counts"], o2["counts"])
+        np.testing.assert_array_equal(o1["vars"], o2["vars"])
+
+
+def test_f16_decode_special_values(orc):
+    bits = np.array([0x0000, 0x8000, 0x0001, 0x03ff, 0x0400, 0x3c00, 0xc000, 0x7bff, 0x7c00, 0xfc00],
+                    dtype=np.uint16)
+    off = np.array([0] + list(range(1, 11)), dtype=np.int64)
+    got, _ = orc.get_in_offsets(bits, off, 0, fmt="f16")
+    want = [0.0, -0.0, 2.0 ** -24, 1023 * 2.0 ** -24, 2.0 ** -14, 1.0, -2.0, 65504.0, np.inf, -np.inf]
+    np.testing.assert_array_equal(got, np.array(want, dtype=np.float32))
+
+
+def test_trijet_exact_tie_goes_to_first(orc):
+    # jets 1, 2, 3 are identical, so triplets (0,1,2), (0,1,3), (0,2,3) tie exactly
+    off = np.array([0, 4], dtype=np.int64)
+    pt = np.array([100, 50, 50, 50], dtype=np.float32)
+    z = np.zeros(4, dtype=np.float32)
+    _m, _pt, idx, gap = orc.max_pt_trijet(pt, z, z, z, off)
+    assert list(idx[0]) == [0, 1, 2] and gap[0] == 0.0
+
+
+def test_chain_dr2_equal_to_cut_keeps_jet(orc):
+    # Delta eta = 0.1f, Delta phi = 0.38729832f give Delta R^2 == 0.16f exactly in
+    # IEEE binary32 (checked here with numpy's float32 arithmetic); "closer than"
+    # is strict, so the jet stays; one float closer it is masked.
+    deta, dphi = F32(0.1), F32(0.38729832)
+    assert deta * deta + dphi * dphi == F32(0.16)
+    closer = np.nextafter(dphi, F32(0))
+    assert deta * deta + closer * closer < F32(0.16)
+    lep = {"pt": 40, "eta": 0.0, "phi": 0.0, "mass": 0.1, "charge": 1, "iso": 0.01, "tight": 1}
+    evs = []
+    for p in (dphi, closer):
+        evs.append({"weight": 1.0, "mu": [lep], "el": [],
+                    "jet": [{"pt": 50, "eta": float(deta), "phi": float(p), "mass": 5, "btag": 0.9},
+                            {"pt": 40, "eta": -2.0, "phi": 2.0, "mass": 5, "btag": 0.1}]})
+    out = orc.run_chain(synth.hand_batch(evs), synth.CUTS, synth.HIST_SPECS, [0])
+    assert list(out["njet"][0]) == [2, 1]
+    assert list(out["pass"][0]) == [1, 0]
