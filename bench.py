@@ -1,0 +1,377 @@
+"""Benchmark of the fused analysis chain on GB300.
+
+One step = one pass of the whole chain (lepton and jet selection, Delta R
+masking, counts, HT, leading jets, pair and trijet masses, 20 weighted
+histograms) over a resident batch of 10M synthetic events (float32 columns,
+int64 offsets) in one hepacc_run_chain launch. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own batch (weak scaling, no collective in
+the timed region). ``--impl reference`` times the CPU oracle on the host
+cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "plain_10m"
+METRIC = "events/s, fused chain (plain FP32 columns, int64 offsets), 1 GB300"
+N_EVENTS = 10_000_000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="hepacc", choices=["hepacc", "reference"])
+    p.add_argument("--events", type=int, default=N_EVENTS)
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary forms")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(batch) -> int:
+    """Bytes the chain must read once: three offsets arrays, the 15 object
+    columns it uses and the event weights."""
+    tot = sum(a.nbytes for a in batch.offsets.values())
+    for name in ("jet_pt", "jet_eta", "jet_phi", "jet_mass", "jet_btag", "mu_pt", "mu_eta", "mu_phi", "mu_iso",
+                 "mu_tight", "el_pt", "el_eta", "el_phi", "el_iso", "el_tight"):
+        tot += batch.cols[name].nbytes
+    return tot + batch.weight.nbytes
+
+
+def chain_traffic(kernel_src_sha):
+    """DRAM bytes per launch of the chain kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "chain_plain_10m.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_src_sha:
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1906_06242_gb300", "csrc")
+    for fn in ("chain.cu", "hepacc_tiles.cuh", "hepacc_device.cuh"):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t0 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def elapsed(self):
+        return time.time() - self.t0
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(batch, n_sample, shifts=(0,)):
+    """The oracle, as it is, on a bounded sample of the workload (the first
+    n_sample events), single-threaded on the host."""
+    from oracle import oracle
+    from paper_1906_06242_gb300 import synth
+    n = min(n_sample, batch.n_events)
+    sub = synth.EventBatch(n_events=n, jet_offsets=batch.jet_offsets[:n + 1], mu_offsets=batch.mu_offsets[:n + 1],
+                           el_offsets=batch.el_offsets[:n + 1], cols=batch.cols, weight=batch.weight[:n])
+    t0 = time.perf_counter()
+    oracle.run_chain(sub, synth.CUTS, synth.HIST_SPECS, list(shifts), per_event=False)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} events of the {batch.n_events}-event workload, {len(shifts)} variation(s), "
+                      f"{dt:.2f} s single-threaded"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1906_06242_gb300 import synth
+    per_step = 300_000
+    batch = synth.generate(per_step, 1)
+    from oracle import oracle
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.run_chain(batch, synth.CUTS, synth.HIST_SPECS, [0], per_event=False)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "events_per_step_sample": per_step},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} events of the {WORKLOAD} generator per step"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1906_06242_gb300 import hepacc as H
+    from paper_1906_06242_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    H.load()
+
+    batch = synth.generate(args.events, 1 + rank)
+    cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [1.0])
+    db = H.DeviceBatch.from_host(batch)
+    out = H.ChainOutputs(cfg, batch.n_events, per_event=False, sumw2=True)
+    structs = (db.c_struct(), cfg.c_struct(), out.c_struct())
+    stream = torch.cuda.current_stream()
+    alg_bytes = algorithmic_bytes(batch)
+
+    def step():
+        H.hepacc_run_chain(db, cfg, out, stream=stream, _structs=structs)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clock = ClockSampler(local)
+    clock.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    # keep the same work running until the clock sampler has seen >= 1 s of load
+    while clock.elapsed() < 1.2:
+        for _ in range(50):
+            step()
+        torch.cuda.synchronize()
+    clocks = clock.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        # the one exchange of the sharded chain: sum of the histograms
+        dist.all_reduce(out.counts)
+        dist.all_reduce(out.sumw)
+    ms_per_step = total_ms / args.steps
+    value = world * batch.n_events / (ms_per_step * 1e-3)
+    avg_kernel_ms = sum(kern_ms) / len(kern_ms)
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / (avg_kernel_ms * 1e-3) / 1e9
+
+    # end to end: pinned host columns -> device, chain, histograms -> host
+    e2e = None
+    if True:
+        pinned = {}
+        for k, a in list(batch.offsets.items()):
+            pinned["off_" + k] = torch.from_numpy(a).pin_memory()
+        for name in H.COLUMNS:
+            pinned[name] = torch.from_numpy(batch.cols[name]).pin_memory()
+        pinned["weight"] = torch.from_numpy(batch.weight).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in pinned.values())
+        res_host = [torch.empty_like(out.counts, device="cpu").pin_memory(),
+                    torch.empty_like(out.sumw, device="cpu").pin_memory(),
+                    torch.empty_like(out.sumw2, device="cpu").pin_memory()]
+        d2h = sum(t.numel() * t.element_size() for t in res_host)
+        dev_bufs = {k: torch.empty_like(t, device="cuda") for k, t in pinned.items()}
+        db2 = H.DeviceBatch(batch.n_events, {k: dev_bufs["off_" + k] for k in ("jet", "mu", "el")},
+                            {name: dev_bufs[name] for name in H.COLUMNS}, dev_bufs["weight"])
+        out2 = H.ChainOutputs(cfg, batch.n_events, per_event=False, sumw2=True)
+        s2 = (db2.c_struct(), cfg.c_struct(), out2.c_struct())
+
+        def e2e_step():
+            for k, t in pinned.items():
+                dev_bufs[k].copy_(t, non_blocking=True)
+            out2.zero_()
+            H.hepacc_run_chain(db2, cfg, out2, stream=stream, _structs=s2)
+            res_host[0].copy_(out2.counts, non_blocking=True)
+            res_host[1].copy_(out2.sumw, non_blocking=True)
+            res_host[2].copy_(out2.sumw2, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(3, min(args.steps, 20))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / k2
+        e2e = {"value": world * batch.n_events / (e2e_ms * 1e-3), "unit": "events/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = secondary_forms(H, synth, batch, torch, stream)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline(batch, 4_000_000) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_gpu": batch.n_events, "offsets": "int64",
+                   "columns": "float32", "variations": 1, "histograms": 20, "bins": 100,
+                   "l2": "inputs larger than L2 (no flush needed)", "input_bytes": int(alg_bytes),
+                   "parallelism": f"dp{world} (independent event shards)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": chain_traffic(kernel_source_sha()), "kernel": "k_chain",
+                     "algorithmic_bytes_per_launch": int(alg_bytes),
+                     "avg_kernel_ms": avg_kernel_ms},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if extra:
+        line["forms"] = extra
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def secondary_forms(H, synth, batch, torch, stream):
+    """The other forms of the headline metric, each timed the same way:
+    the chain as separate per-operation calls (FP32), the fused chain on
+    BF16 kinematic columns."""
+    from paper_1906_06242_gb300 import perop
+    res = {}
+    cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [1.0])
+
+    def timeit(fn, k=10, w=2):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    db = H.DeviceBatch.from_host(batch)
+    out = H.ChainOutputs(cfg, batch.n_events, per_event=False)
+    ws = perop.PerOpWorkspace(db)
+    ms = timeit(lambda: perop.run_chain_per_op(db, cfg, out, ws, stream=stream), k=5, w=1)
+    res["per_op_fp32"] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms}
+    del ws, db
+    for fmt in ("bf16", "f16"):
+        hb = synth.reduced_precision(batch, fmt)
+        dh = H.DeviceBatch.from_host(hb)
+        oh = H.ChainOutputs(cfg, batch.n_events, per_event=False)
+        s = (dh.c_struct(), cfg.c_struct(), oh.c_struct())
+        ms = timeit(lambda: H.hepacc_run_chain(dh, cfg, oh, stream=stream, _structs=s), k=20, w=3)
+        nbytes = algorithmic_bytes(hb)
+        res[f"fused_{fmt}"] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms,
+                               "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}
+        del dh
+    return res
+
+
+if __name__ == "__main__":
+    main()

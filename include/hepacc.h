@@ -1,0 +1,301 @@
+/*
+ * hepacc: GPU kernels for columnar (jagged-array) collider event data.
+ *
+ * Operations from "Processing Columnar Collider Data with GPU-Accelerated
+ * Kernels" (Pata & Spiropulu, arXiv:1906.06242), written for NVIDIA GB300
+ * (sm_103a).
+ *
+ * Data model (Section II). N events with M objects of one collection are an
+ * offsets array of N+1 entries plus one flat content array of M entries per
+ * feature; event i owns elements [offsets[i], offsets[i+1]). offsets[0] may be
+ * non-zero (a slice of a larger batch); offsets must be non-decreasing.
+ * Event masks (mask_rows, N bytes) and content masks (mask_content, M bytes)
+ * are uint8 arrays, non-zero meaning "selected" (Section III); a NULL mask
+ * selects everything.
+ *
+ * Conventions for every call below.
+ *  - Pointers to arrays are DEVICE pointers owned by the caller, unless the
+ *    call says otherwise; the library keeps no reference after the call
+ *    returns and frees nothing. Per-operation calls allocate no memory.
+ *  - Calls are asynchronous: they validate their scalar arguments on the
+ *    host, enqueue work on `stream` (NULL = the legacy default stream) and
+ *    return. A non-OK status means nothing was enqueued, except
+ *    HEPACC_ERR_CUDA, returned when a launch failed.
+ *  - Content columns are read in whole 16-byte-aligned chunks: up to 15
+ *    bytes before the first and after the last element of an event block
+ *    may be read (never written, never used). Such a chunk never leaves the
+ *    memory page of a valid element.
+ *  - Local indices are 0-based inside the event; -1 means "none".
+ *  - hepacc_last_error() describes the most recent failing call made on the
+ *    calling host thread.
+ */
+#ifndef HEPACC_H
+#define HEPACC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the runtime's stream handle type). */
+typedef struct CUstream_st *hepacc_stream;
+
+typedef enum {
+    HEPACC_OK = 0,
+    HEPACC_ERR_INVALID_ARG = 1,   /* NULL required pointer, negative size, bad bins ... */
+    HEPACC_ERR_DTYPE = 2,         /* unsupported element type for this call */
+    HEPACC_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    HEPACC_ERR_OOM = 4,           /* a plan could not allocate its workspace */
+    HEPACC_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    HEPACC_ERR_DEVICE_CHECK = 6   /* device-side validation found bad input */
+} hepacc_status;
+
+typedef enum {
+    HEPACC_F32 = 0,
+    HEPACC_F16 = 1,
+    HEPACC_BF16 = 2,
+    HEPACC_I8 = 3,
+    HEPACC_U8 = 4,
+    HEPACC_I32 = 5,
+    HEPACC_I64 = 6,
+    HEPACC_F64 = 7
+} hepacc_dtype;
+
+/* ---------------------------------------------------------------------------
+ * Library state and diagnostics
+ * ------------------------------------------------------------------------- */
+
+/* Version string of the library; static storage. */
+const char *hepacc_version(void);
+
+/* Text of the last failing call on this host thread ("" if none); valid until
+ * the next failing call on the same thread. */
+const char *hepacc_last_error(void);
+
+/* Name of a status code; static storage. */
+const char *hepacc_status_string(hepacc_status s);
+
+/* Reads and clears the device error word of the current device, which
+ * kernels set when a bounded wait gives up (bit 0) or a device-side check
+ * fails (bit 1). Synchronises the device. *flags receives the word. */
+hepacc_status hepacc_device_error(uint32_t *flags);
+
+/* Offsets check (Section II layout): offsets[0] >= 0, non-decreasing, and
+ * offsets[n_rows] <= content_len. *first_bad (a DEVICE int64) receives the
+ * smallest event index i whose offsets[i+1] breaks a rule (-1 if none; -2 if
+ * offsets[0] < 0). offsets_type is HEPACC_I32 or HEPACC_I64. Asynchronous. */
+hepacc_status hepacc_validate_offsets(const void *offsets, hepacc_dtype offsets_type, int64_t n_rows,
+                                      int64_t content_len, int64_t *first_bad, hepacc_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Generic kernels over jagged arrays (Section III)
+ * ------------------------------------------------------------------------- */
+
+/* sum_in_offsets (Section III, Listing 1). For every event i with
+ * mask_rows[i] set: out[i] += content[j] for each j in [offsets[i],
+ * offsets[i+1]) with mask_content[j] set, one element at a time in element
+ * order. Events with mask_rows[i] unset keep their value of out[i]; with
+ * out zero-filled the result is the plain sum.
+ * content_type F32, F16 or BF16: out_type must be F32 and every addition is
+ * an IEEE binary32 addition (half inputs widened exactly).
+ * content_type U8, I8, I32: out_type I32 or I64 (counting selected objects by
+ * summing masks); I64 content needs out_type I64. */
+hepacc_status hepacc_sum_in_offsets(const void *content, hepacc_dtype content_type, const void *offsets,
+                                    hepacc_dtype offsets_type, int64_t n_rows, const uint8_t *mask_rows,
+                                    const uint8_t *mask_content, void *out, hepacc_dtype out_type,
+                                    hepacc_stream stream);
+
+/* max_in_offsets / min_in_offsets (Section III). For every event i with
+ * mask_rows[i] set: out[i] = the largest (smallest) masked-in non-NaN value,
+ * out_arg[i] = its local index (first occurrence on ties); with no such
+ * element out[i] = empty_value and out_arg[i] = -1. content_type F32, F16,
+ * BF16, U8, I8 or I32 (compared as float). out or out_arg may be NULL (not
+ * both). Events with mask_rows[i] unset are untouched. */
+hepacc_status hepacc_max_in_offsets(const void *content, hepacc_dtype content_type, const void *offsets,
+                                    hepacc_dtype offsets_type, int64_t n_rows, const uint8_t *mask_rows,
+                                    const uint8_t *mask_content, float empty_value, float *out,
+                                    int32_t *out_arg, hepacc_stream stream);
+hepacc_status hepacc_min_in_offsets(const void *content, hepacc_dtype content_type, const void *offsets,
+                                    hepacc_dtype offsets_type, int64_t n_rows, const uint8_t *mask_rows,
+                                    const uint8_t *mask_content, float empty_value, float *out,
+                                    int32_t *out_arg, hepacc_stream stream);
+
+/* get_in_offsets (Section III). For every event i with mask_rows[i] set:
+ * the n-th masked-in element (n counted from 0 over elements with
+ * mask_content set), n = nth[i] if nth (DEVICE int32[n_rows]) is non-NULL,
+ * else nth_scalar. out[i] = its value as float, out_index[i] = its local
+ * index; if n < 0 or the event has too few such elements, out[i] =
+ * default_value and out_index[i] = -1. Either output may be NULL (not both).
+ * content_type as for max_in_offsets. */
+hepacc_status hepacc_get_in_offsets(const void *content, hepacc_dtype content_type, const void *offsets,
+                                    hepacc_dtype offsets_type, int64_t n_rows, const int32_t *nth,
+                                    int32_t nth_scalar, const uint8_t *mask_rows,
+                                    const uint8_t *mask_content, float default_value, float *out,
+                                    int32_t *out_index, hepacc_stream stream);
+
+/* set_in_offsets (Section III). For every event i with mask_rows[i] set,
+ * the n-th masked-in element (as in get_in_offsets) of content is set to
+ * value (converted to the content type); events without such an element are
+ * unchanged. content_type U8 (a mask, e.g. keep the first two jets) or F32.
+ * content is modified in place. */
+hepacc_status hepacc_set_in_offsets(void *content, hepacc_dtype content_type, const void *offsets,
+                                    hepacc_dtype offsets_type, int64_t n_rows, const int32_t *nth,
+                                    int32_t nth_scalar, const uint8_t *mask_rows,
+                                    const uint8_t *mask_content, double value, hepacc_stream stream);
+
+/* Object selection by a cut (Section IV: object selection on pt, eta):
+ * mask_out[j] = mask_in[j] && lo < v && v < hi for j < n, with
+ * v = content[j] * scale as one binary32 product (|v| when use_abs != 0).
+ * NaN never passes. content_type F32, F16, BF16, U8, I8 or I32. mask_in may
+ * be NULL and may equal mask_out. */
+hepacc_status hepacc_select_range(const void *content, hepacc_dtype content_type, int64_t n, float scale,
+                                  float lo, float hi, int use_abs, const uint8_t *mask_in,
+                                  uint8_t *mask_out, hepacc_stream stream);
+
+/* out[j] = content[j] * scale (one binary32 product) for j < n: a jet
+ * energy-scale variation (Section IV). content_type F32, F16 or BF16. */
+hepacc_status hepacc_scale(const void *content, hepacc_dtype content_type, int64_t n, float scale,
+                           float *out, hepacc_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Specialised kernels (Section III)
+ * ------------------------------------------------------------------------- */
+
+/* mask_deltar_first (Section III): for every event i with mask_rows[i] set
+ * and every object j of collection 1 in it, mask1_out[j] = mask1_in[j] and
+ * no masked-in object k of collection 2 in the same event has
+ * Delta R^2 = Delta eta^2 + Delta phi^2 < dr2_cut, with Delta phi folded into
+ * [-pi, pi] by one shift of 2 pi and the sum of two rounded binary32
+ * squares (no fused multiply-add). Events with mask_rows[i] unset keep
+ * mask1_out. Both collections have n_rows events and offsets of the same
+ * type; eta/phi of one collection share one type (F32, F16 or BF16).
+ * mask1_in, mask2 may be NULL; mask1_out must not alias mask1_in unless
+ * equal. */
+hepacc_status hepacc_mask_deltar(const void *eta1, const void *phi1, hepacc_dtype type1, const void *offsets1,
+                                 const void *eta2, const void *phi2, hepacc_dtype type2, const void *offsets2,
+                                 hepacc_dtype offsets_type, int64_t n_rows, const uint8_t *mask_rows,
+                                 const uint8_t *mask1_in, const uint8_t *mask2, float dr2_cut,
+                                 uint8_t *mask1_out, hepacc_stream stream);
+
+/* fill_histogram (Section III): for j < n with mask[j] set and data[j] not
+ * NaN, bin b of data[j] against the binary32 edges[0..nbins] (increasing):
+ * b = 0 if v < edges[0], nbins+1 if v >= edges[nbins], else the b with
+ * edges[b-1] <= v < edges[b]. Accumulates counts[b] += 1, sumw[b] += w,
+ * sumw2[b] += w*w with w = weights[j] (1 if weights is NULL), sums in
+ * binary64. counts, sumw have nbins+2 entries; sumw and sumw2 may be NULL.
+ * 1 <= nbins <= 65536. data_type F32, F16, BF16, U8, I8 or I32. The order
+ * of the binary64 additions is unspecified. */
+hepacc_status hepacc_fill_histogram(const void *data, hepacc_dtype data_type, const float *weights,
+                                    const uint8_t *mask, int64_t n, const float *edges, int32_t nbins,
+                                    uint64_t *counts, double *sumw, double *sumw2, hepacc_stream stream);
+
+/* Invariant mass of a pair of objects per event (Section IV: high-level
+ * variables). For every event i with mask_rows[i] set: out[i] = mass of the
+ * sum of the four-momenta of the objects at local indices idx_a[i] and
+ * idx_b[i] (from pt, eta, phi, mass), NaN if an index is negative or outside
+ * the event. Computed in binary32 through a form without cancellation
+ * (relative error below 1e-5). type F32, F16 or BF16 for all four columns. */
+hepacc_status hepacc_pair_mass(const void *pt, const void *eta, const void *phi, const void *mass,
+                               hepacc_dtype type, const void *offsets, hepacc_dtype offsets_type,
+                               int64_t n_rows, const int32_t *idx_a, const int32_t *idx_b,
+                               const uint8_t *mask_rows, float *out, hepacc_stream stream);
+
+/* Trijet candidate (Section IV: top quark candidate from a jet triplet).
+ * For every event i with mask_rows[i] set: among triplets a<b<c of masked-in
+ * objects, the one with the largest |pT_a + pT_b + pT_c| (transverse
+ * vectors; first in lexicographic order on ties); out_mass[i] its invariant
+ * mass, out_pt[i] that |sum pT|, out_idx3[3i..3i+2] the local indices. Fewer
+ * than three objects: NaN, NaN, -1 -1 -1. Any output may be NULL. */
+hepacc_status hepacc_max_pt_trijet(const void *pt, const void *eta, const void *phi, const void *mass,
+                                   hepacc_dtype type, const void *offsets, hepacc_dtype offsets_type,
+                                   int64_t n_rows, const uint8_t *mask_rows, const uint8_t *mask_content,
+                                   float *out_mass, float *out_pt, int32_t *out_idx3,
+                                   hepacc_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * The fused analysis chain (Section IV benchmark analysis), one launch
+ * ------------------------------------------------------------------------- */
+
+#define HEPACC_CHAIN_NVARS 20
+#define HEPACC_MAX_VARIATIONS 64
+#define HEPACC_CHAIN_MAX_EDGES 4096
+
+/* One sample of events: three collections (jets, muons, electrons) sharing
+ * n_events and one offsets type. kin_type (F32, F16, BF16) is the type of
+ * pt, eta, phi, mass of all collections; btag_type F32 or F16. Lepton iso is
+ * float32 and tight uint8. All pointers DEVICE. */
+typedef struct {
+    int64_t n_events;
+    hepacc_dtype offsets_type;
+    const void *jet_offsets, *mu_offsets, *el_offsets;
+    hepacc_dtype kin_type;
+    hepacc_dtype btag_type;
+    const void *jet_pt, *jet_eta, *jet_phi, *jet_mass, *jet_btag;
+    const void *mu_pt, *mu_eta, *mu_phi;
+    const float *mu_iso;
+    const uint8_t *mu_tight;
+    const void *el_pt, *el_eta, *el_phi;
+    const float *el_iso;
+    const uint8_t *el_tight;
+    const float *weight;
+} hepacc_event_batch;
+
+/* Cuts, jet-pt scale variations and the 20 histograms. HOST memory: the call
+ * copies what it needs. Histogram h has nbins[h] bins and nbins[h]+1
+ * increasing binary32 edges, stored one histogram after another in edges;
+ * its bins (with underflow and overflow, nbins[h]+2 of them) start at
+ * sum over h' < h of (nbins[h'] + 2) inside one variation's histogram block
+ * of total_bins = sum of (nbins[h] + 2) entries. */
+typedef struct {
+    float lep_pt_min, lep_abseta_max, lep_iso_max;
+    float jet_pt_min, jet_abseta_max, dr2_cut, btag_min;
+    int32_t n_var;                         /* 1 .. HEPACC_MAX_VARIATIONS */
+    const float *scales;                   /* [n_var] jet-pt scale factors */
+    int32_t nbins[HEPACC_CHAIN_NVARS];
+    const float *edges;                    /* sum (nbins[h]+1) <= HEPACC_CHAIN_MAX_EDGES */
+} hepacc_chain_config;
+
+/* Outputs, DEVICE memory. counts, sumw (and sumw2 if non-NULL) are
+ * [n_var][total_bins] and accumulate (+=), so batches add up. The per-event
+ * arrays are optional (NULL = not written); when any is given, every
+ * variable is evaluated for every event:
+ *   ev_pass [n_var][N] uint8, ev_nlep [N], ev_njet and ev_nb [n_var][N],
+ *   ev_idx [n_var][5][N] local indices (leading, sub-leading, trijet a, b, c),
+ *   ev_vars [n_var][20][N] the histogram variables, NaN where undefined. */
+typedef struct {
+    uint64_t *counts;
+    double *sumw;
+    double *sumw2;
+    uint8_t *ev_pass;
+    int32_t *ev_nlep;
+    int32_t *ev_njet, *ev_nb;
+    int32_t *ev_idx;
+    float *ev_vars;
+} hepacc_chain_outputs;
+
+/* The Section IV chain for every event and every variation k (scale s_k):
+ *  1. leptons (muons and electrons) selected by pt > lep_pt_min,
+ *     |eta| < lep_abseta_max, tight != 0, iso < lep_iso_max; n_lep counts
+ *     both; "the lepton" is the first selected muon, else electron;
+ *  2. jets: pt_k = pt * s_k (binary32); selected if pt_k > jet_pt_min,
+ *     |eta| < jet_abseta_max and Delta R^2 >= dr2_cut (as in
+ *     hepacc_mask_deltar) to every selected lepton;
+ *  3. n_jet, n_b (btag > btag_min); pass = n_lep == 1, n_jet >= 2, n_b >= 1;
+ *  4. the 20 variables, in order: HT (binary32 sum of pt_k in element
+ *     order), leading-jet pt_k, eta, phi, mass, btag, sub-leading pt_k,
+ *     dijet mass of the two leading jets, n_jet, n_b, max btag, trijet mass
+ *     and |sum pT| (max-|sum pT| triplet, n_jet >= 3), lepton pt, eta, phi,
+ *     iso, ST = HT + lepton pt, sum of selected-jet masses, event weight;
+ *  5. every passing event adds its weight to one bin of each histogram
+ *     (the trijet ones only when n_jet >= 3).
+ * One kernel launch; each input column is read once. */
+hepacc_status hepacc_run_chain(const hepacc_event_batch *batch, const hepacc_chain_config *config,
+                               const hepacc_chain_outputs *out, hepacc_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEPACC_H */

@@ -1,0 +1,798 @@
+// Per-operation kernels (Section III of arXiv:1906.06242): segmented sum,
+// max/min, get/set within offsets, Delta R masking, trijet and pair masses,
+// object selection, scaling and weighted histogram filling, with their C-ABI
+// entry points.
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+#include "hepacc_host.h"
+#include "hepacc_tiles.cuh"
+
+namespace hepacc {
+
+unsigned int tu_error_ops(bool clear) {
+    unsigned int v = 0;
+    cudaMemcpyFromSymbol(&v, g_device_error, sizeof v);
+    if (clear && v) {
+        unsigned int z = 0;
+        cudaMemcpyToSymbol(g_device_error, &z, sizeof z);
+    }
+    return v;
+}
+
+namespace {
+
+constexpr int kBlock = 256;             // 8 warps
+constexpr int kCapElems = 512;          // stage capacity per column, elements (32 events x 16)
+constexpr int NC = 6;                   // columns per stage at most
+using Spec = StageSpec<NC>;
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<uint8_t> { using type = int64_t; };
+template <> struct Acc<int8_t> { using type = int64_t; };
+template <> struct Acc<int32_t> { using type = int64_t; };
+template <> struct Acc<int64_t> { using type = int64_t; };
+
+template <typename AccT, typename T>
+__device__ __forceinline__ AccT acc_add(AccT a, T x) { return a + static_cast<AccT>(x); }
+template <>
+__device__ __forceinline__ float acc_add<float, float>(float a, float x) { return __fadd_rn(a, x); }
+template <>
+__device__ __forceinline__ float acc_add<float, __half>(float a, __half x) { return __fadd_rn(a, __half2float(x)); }
+template <>
+__device__ __forceinline__ float acc_add<float, __nv_bfloat16>(float a, __nv_bfloat16 x) {
+    return __fadd_rn(a, __bfloat162float(x));
+}
+
+// sum_in_offsets (Listing 1): out[e] += masked elements in element order.
+// Columns: 0 = content, 1 = mask_content.
+template <typename T, typename OffT, typename OutT>
+__global__ void __launch_bounds__(kBlock) k_sum(Spec spec, const OffT* off, int64_t n,
+                                                const uint8_t* __restrict__ mask_rows, OutT* __restrict__ out) {
+    const OffT* const offs[1] = {off};
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
+        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
+        using A = typename Acc<T>::type;
+        A acc = static_cast<A>(out[v.e]);
+        const bool hm = v.colp[1] != nullptr;
+        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
+            if (hm && !v.template at<uint8_t>(1, 0, i)) continue;
+            acc = acc_add<A, T>(acc, v.template at<T>(0, 0, i));
+        }
+        out[v.e] = static_cast<OutT>(acc);
+    });
+}
+
+// max/min_in_offsets: first occurrence of the extreme non-NaN masked value.
+template <typename T, typename OffT, bool MAX>
+__global__ void __launch_bounds__(kBlock) k_minmax(Spec spec, const OffT* off, int64_t n,
+                                                   const uint8_t* __restrict__ mask_rows, float empty,
+                                                   float* __restrict__ out, int32_t* __restrict__ arg) {
+    const OffT* const offs[1] = {off};
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
+        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
+        const bool hm = v.colp[1] != nullptr;
+        int64_t bi = -1;
+        float best = empty;
+        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
+            if (hm && !v.template at<uint8_t>(1, 0, i)) continue;
+            const float x = Elem<T>::f(v.template at<T>(0, 0, i));
+            if (x != x) continue;
+            if (bi < 0 || (MAX ? x > best : x < best)) {
+                best = x;
+                bi = i;
+            }
+        }
+        if (out) out[v.e] = bi < 0 ? empty : best;
+        if (arg) arg[v.e] = bi < 0 ? -1 : static_cast<int32_t>(bi - v.s[0]);
+    });
+}
+
+// get_in_offsets: the n-th masked-in element.
+template <typename T, typename OffT>
+__global__ void __launch_bounds__(kBlock) k_get(Spec spec, const OffT* off, int64_t n,
+                                                const int32_t* __restrict__ nth, int32_t nth_scalar,
+                                                const uint8_t* __restrict__ mask_rows, float dflt,
+                                                float* __restrict__ out, int32_t* __restrict__ oidx) {
+    const OffT* const offs[1] = {off};
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
+        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
+        const bool hm = v.colp[1] != nullptr;
+        const int64_t want = nth ? nth[v.e] : nth_scalar;
+        int64_t seen = 0, found = -1;
+        if (want >= 0) {
+            for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
+                if (hm && !v.template at<uint8_t>(1, 0, i)) continue;
+                if (seen == want) {
+                    found = i;
+                    break;
+                }
+                ++seen;
+            }
+        }
+        if (out) out[v.e] = found < 0 ? dflt : Elem<T>::f(v.template at<T>(0, 0, found));
+        if (oidx) oidx[v.e] = found < 0 ? -1 : static_cast<int32_t>(found - v.s[0]);
+    });
+}
+
+// mask_deltar_first. Columns: 0 eta1, 1 phi1, 2 mask1_in (collection 0);
+// 3 eta2, 4 phi2, 5 mask2 (collection 1).
+template <typename T1, typename T2, typename OffT>
+__global__ void __launch_bounds__(kBlock) k_deltar(Spec spec, const OffT* off1, const OffT* off2, int64_t n,
+                                                   const uint8_t* __restrict__ mask_rows, float cut,
+                                                   uint8_t* __restrict__ mask_out) {
+    const OffT* const offs[2] = {off1, off2};
+    tile_loop<OffT, 2, NC>(spec, offs, n, [&](const TileView<2, NC>& v) {
+        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
+        const bool h1 = v.colp[2] != nullptr, h2 = v.colp[5] != nullptr;
+        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
+            bool keep = h1 ? v.template at<uint8_t>(2, 0, i) != 0 : true;
+            if (keep) {
+                const float e1 = Elem<T1>::f(v.template at<T1>(0, 0, i));
+                const float p1 = Elem<T1>::f(v.template at<T1>(1, 0, i));
+                for (int64_t j = v.s[1]; j < v.t[1]; ++j) {
+                    if (h2 && !v.template at<uint8_t>(5, 1, j)) continue;
+                    const float d = dr2_f32(e1, p1, Elem<T2>::f(v.template at<T2>(3, 1, j)),
+                                            Elem<T2>::f(v.template at<T2>(4, 1, j)));
+                    if (d < cut) {
+                        keep = false;
+                        break;
+                    }
+                }
+            }
+            mask_out[i] = keep ? 1 : 0;
+        }
+    });
+}
+
+// Trijet: max |sum pT| over triplets of masked-in objects, its mass.
+// Columns: 0 pt, 1 eta, 2 phi, 3 mass, 4 mask.
+constexpr int kTriLocal = 24;
+
+template <typename T, typename OffT>
+__global__ void __launch_bounds__(kBlock) k_trijet(Spec spec, const OffT* off, int64_t n,
+                                                   const uint8_t* __restrict__ mask_rows, float* __restrict__ om,
+                                                   float* __restrict__ opt, int32_t* __restrict__ oidx) {
+    const OffT* const offs[1] = {off};
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
+        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
+        const bool hm = v.colp[4] != nullptr;
+        float px[kTriLocal], py[kTriLocal];
+        int32_t li[kTriLocal];
+        int cnt = 0;
+        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
+            if (hm && !v.template at<uint8_t>(4, 0, i)) continue;
+            if (cnt < kTriLocal) {
+                float sn, cs;
+                const float pt = Elem<T>::f(v.template at<T>(0, 0, i));
+                sincosf(Elem<T>::f(v.template at<T>(2, 0, i)), &sn, &cs);
+                px[cnt] = pt * cs;
+                py[cnt] = pt * sn;
+                li[cnt] = static_cast<int32_t>(i - v.s[0]);
+            }
+            ++cnt;
+        }
+        int32_t ba = -1, bb = -1, bc = -1;
+        float best = -1.0f;
+        if (cnt >= 3 && cnt <= kTriLocal) {
+            for (int a = 0; a < cnt; ++a)
+                for (int b = a + 1; b < cnt; ++b) {
+                    const float sx = px[a] + px[b], sy = py[a] + py[b];
+                    for (int c = b + 1; c < cnt; ++c) {
+                        const float tx = sx + px[c], ty = sy + py[c];
+                        const float val = tx * tx + ty * ty;
+                        if (val > best) {
+                            best = val;
+                            ba = li[a];
+                            bb = li[b];
+                            bc = li[c];
+                        }
+                    }
+                }
+        } else if (cnt > kTriLocal) {
+            // many objects: enumerate the masked-in elements directly
+            for (int64_t a = v.s[0]; a < v.t[0]; ++a) {
+                if (hm && !v.template at<uint8_t>(4, 0, a)) continue;
+                float sa, ca;
+                sincosf(Elem<T>::f(v.template at<T>(2, 0, a)), &sa, &ca);
+                const float pa = Elem<T>::f(v.template at<T>(0, 0, a));
+                for (int64_t b = a + 1; b < v.t[0]; ++b) {
+                    if (hm && !v.template at<uint8_t>(4, 0, b)) continue;
+                    float sb, cb;
+                    sincosf(Elem<T>::f(v.template at<T>(2, 0, b)), &sb, &cb);
+                    const float pb = Elem<T>::f(v.template at<T>(0, 0, b));
+                    const float sx = pa * ca + pb * cb, sy = pa * sa + pb * sb;
+                    for (int64_t c = b + 1; c < v.t[0]; ++c) {
+                        if (hm && !v.template at<uint8_t>(4, 0, c)) continue;
+                        float sc, cc;
+                        sincosf(Elem<T>::f(v.template at<T>(2, 0, c)), &sc, &cc);
+                        const float pc = Elem<T>::f(v.template at<T>(0, 0, c));
+                        const float tx = sx + pc * cc, ty = sy + pc * sc;
+                        const float val = tx * tx + ty * ty;
+                        if (val > best) {
+                            best = val;
+                            ba = static_cast<int32_t>(a - v.s[0]);
+                            bb = static_cast<int32_t>(b - v.s[0]);
+                            bc = static_cast<int32_t>(c - v.s[0]);
+                        }
+                    }
+                }
+            }
+        }
+        float m = __int_as_float(0x7fc00000), ptj = m;
+        if (ba >= 0) {
+            MassObj o[3];
+            const int32_t ix[3] = {ba, bb, bc};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int64_t i = v.s[0] + ix[q];
+                o[q] = mass_obj(Elem<T>::f(v.template at<T>(0, 0, i)), Elem<T>::f(v.template at<T>(1, 0, i)),
+                                Elem<T>::f(v.template at<T>(2, 0, i)), Elem<T>::f(v.template at<T>(3, 0, i)));
+            }
+            m = mass3obj(o[0], o[1], o[2]);
+            ptj = sqrtf(best);
+        }
+        if (om) om[v.e] = m;
+        if (opt) opt[v.e] = ptj;
+        if (oidx) {
+            oidx[3 * v.e] = ba;
+            oidx[3 * v.e + 1] = bb;
+            oidx[3 * v.e + 2] = bc;
+        }
+    });
+}
+
+template <typename T, typename OffT>
+__global__ void __launch_bounds__(kBlock) k_pair_mass(const T* pt, const T* eta, const T* phi, const T* mass,
+                                                      const OffT* off, int64_t n, const int32_t* ia,
+                                                      const int32_t* ib, const uint8_t* mask_rows, float* out) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask_rows && !mask_rows[e]) continue;
+        const int64_t i0 = ldoff(off, e), cnt = ldoff(off, e + 1) - i0;
+        const int64_t a = ia[e], b = ib[e];
+        if (a < 0 || b < 0 || a >= cnt || b >= cnt) {
+            out[e] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const MassObj oa = mass_obj(ldf(pt, i0 + a), ldf(eta, i0 + a), ldf(phi, i0 + a), ldf(mass, i0 + a));
+        const MassObj ob = mass_obj(ldf(pt, i0 + b), ldf(eta, i0 + b), ldf(phi, i0 + b), ldf(mass, i0 + b));
+        out[e] = mass2obj(oa, ob);
+    }
+}
+
+template <typename T, typename OffT>
+__global__ void __launch_bounds__(kBlock) k_set(T* x, const OffT* off, int64_t n, const int32_t* nth, int32_t nth_scalar,
+                                                const uint8_t* mask_rows, const uint8_t* mask_content, T value) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask_rows && !mask_rows[e]) continue;
+        const int64_t want = nth ? nth[e] : nth_scalar;
+        if (want < 0) continue;
+        int64_t seen = 0;
+        for (int64_t i = ldoff(off, e); i < ldoff(off, e + 1); ++i) {
+            if (mask_content && !mask_content[i]) continue;
+            if (seen == want) {
+                x[i] = value;
+                break;
+            }
+            ++seen;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_select(const T* x, int64_t n, float scale, float lo, float hi, int use_abs,
+                                                   const uint8_t* min, uint8_t* mout) {
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float v = __fmul_rn(ldf(x, j), scale);
+        if (use_abs) v = fabsf(v);
+        const bool in = min ? min[j] != 0 : true;
+        mout[j] = (in && v > lo && v < hi) ? 1 : 0;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_scale(const T* x, int64_t n, float s, float* out) {
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[j] = __fmul_rn(ldf(x, j), s);
+}
+
+// fill_histogram with a block-private copy of the histogram in shared memory:
+// edges, u32 counts, f64 sums. Lanes that hit the same bin are merged first
+// (__match_any_sync) so one lane per bin does the shared-memory atomics; the
+// block adds its histogram to global memory at the end.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_hist_smem(const T* x, const float* w, const uint8_t* mask, int64_t n,
+                                                      const float* edges, int nb,
+                                                      unsigned long long* counts, double* sumw, double* sumw2) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nbin = nb + 2;
+    double* s_w = reinterpret_cast<double*>(smem);
+    double* s_w2 = s_w + nbin;
+    double* s_lane = s_w2 + nbin;
+    unsigned int* s_c = reinterpret_cast<unsigned int*>(s_lane + blockDim.x);
+    float* s_e = reinterpret_cast<float*>(s_c + nbin);
+    for (int i = threadIdx.x; i < nbin; i += blockDim.x) {
+        s_w[i] = 0.0;
+        s_w2[i] = 0.0;
+        s_c[i] = 0u;
+    }
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x) s_e[i] = edges[i];
+    __syncthreads();
+    const float span = s_e[nb] - s_e[0];
+    const float inv_width = span > 0.0f ? static_cast<float>(nb) / span : 0.0f;
+    const int lane = threadIdx.x & 31;
+    double* my = s_lane + (threadIdx.x & ~31);
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += step) {
+        const int64_t j = base + lane;
+        int b = -1;
+        double ww = 0.0;
+        if (j < n && (!mask || mask[j])) {
+            b = find_bin(ldf(x, j), s_e, nb, inv_width);
+            ww = w ? static_cast<double>(w[j]) : 1.0;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        my[lane] = ww;
+        __syncwarp();
+        if (b >= 0 && lane == __ffs(peers) - 1) {
+            double sw = 0.0, sw2 = 0.0;
+            for (unsigned m = peers; m; m &= m - 1) {
+                const double q = my[__ffs(m) - 1];
+                sw += q;
+                sw2 += q * q;
+            }
+            atomicAdd(&s_c[b], static_cast<unsigned>(__popc(peers)));
+            if (sumw) atomicAdd(&s_w[b], sw);
+            if (sumw2) atomicAdd(&s_w2[b], sw2);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbin; i += blockDim.x) {
+        if (s_c[i] == 0u) continue;
+        atomicAdd(&counts[i], static_cast<unsigned long long>(s_c[i]));
+        if (sumw) atomicAdd(&sumw[i], s_w[i]);
+        if (sumw2) atomicAdd(&sumw2[i], s_w2[i]);
+    }
+}
+
+// fill_histogram straight into global memory (histograms too large for
+// shared memory).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_hist_global(const T* x, const float* w, const uint8_t* mask, int64_t n,
+                                                        const float* edges, int nb,
+                                                        unsigned long long* counts, double* sumw, double* sumw2) {
+    const float span = edges[nb] - edges[0];
+    const float inv_width = span > 0.0f ? static_cast<float>(nb) / span : 0.0f;
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask && !mask[j]) continue;
+        const int b = find_bin(ldf(x, j), edges, nb, inv_width);
+        if (b < 0) continue;
+        const double ww = w ? static_cast<double>(w[j]) : 1.0;
+        atomicAdd(&counts[b], 1ull);
+        if (sumw) atomicAdd(&sumw[b], ww);
+        if (sumw2) atomicAdd(&sumw2[b], ww * ww);
+    }
+}
+
+template <typename OffT>
+__global__ void k_validate(const OffT* off, int64_t n, int64_t m, unsigned long long* first_bad) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t a = ldoff(off, i), b = ldoff(off, i + 1);
+        if (b < a || (i + 1 == n && b > m)) atomicMin(first_bad, static_cast<unsigned long long>(i));
+    }
+}
+
+__global__ void k_validate_init(const void* off, int ot64, unsigned long long* first_bad) {
+    *first_bad = ~0ull;
+    const int64_t o0 = ot64 ? *static_cast<const int64_t*>(off) : *static_cast<const int32_t*>(off);
+    if (o0 < 0) *first_bad = ~0ull - 1;
+}
+
+__global__ void k_validate_fini(unsigned long long* first_bad) {
+    const unsigned long long v = *first_bad;
+    long long r;
+    if (v == ~0ull) r = -1;
+    else if (v == ~0ull - 1) r = -2;
+    else r = static_cast<long long>(v);
+    *reinterpret_cast<long long*>(first_bad) = r;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+
+struct LaunchCache {
+    std::mutex mu;
+    std::unordered_map<const void*, int> smem_set;   // kernel -> dynamic smem attribute set
+};
+LaunchCache& cache() {
+    static LaunchCache c;
+    return c;
+}
+
+// Sets the kernel's dynamic shared memory limit once and returns the grid
+// size for `work` warp tiles (persistent: at most resident blocks x SMs).
+template <typename K>
+hepacc_status tile_grid(K kernel, size_t smem, int64_t ntiles, int* grid) {
+    const DeviceInfo di = device_info();
+    if (smem > static_cast<size_t>(di.smem_optin)) return fail(HEPACC_ERR_INVALID_ARG, "stage buffers exceed shared memory");
+    {
+        std::lock_guard<std::mutex> g(cache().mu);
+        auto it = cache().smem_set.find(reinterpret_cast<const void*>(kernel));
+        if (it == cache().smem_set.end() || it->second < static_cast<int>(smem)) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            cache().smem_set[reinterpret_cast<const void*>(kernel)] = static_cast<int>(smem);
+        }
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) per_sm = 1;
+    const int64_t want = (ntiles + (kBlock / 32) - 1) / (kBlock / 32);
+    *grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(per_sm) * di.sms)));
+    return HEPACC_OK;
+}
+
+inline int flat_grid(int64_t n) {
+    const DeviceInfo di = device_info();
+    const int64_t want = (n + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, static_cast<int64_t>(di.sms) * 8)));
+}
+
+struct SpecBuilder {
+    Spec s{};
+    uint32_t off = 0;
+    SpecBuilder() { s.ncol = 0; }
+    void add(const void* base, size_t es, int coll, int cap_elems = kCapElems) {
+        ColSpec& c = s.col[s.ncol++];
+        c.base = static_cast<const unsigned char*>(base);
+        c.es = static_cast<uint32_t>(es);
+        c.coll = static_cast<uint32_t>(coll);
+        c.cap = base ? static_cast<uint32_t>((cap_elems * es + 32 + 15) & ~size_t(15)) : 0u;
+        c.soff = off;
+        off += c.cap;
+    }
+    Spec done() {
+        s.buf_bytes = (off + 127) & ~uint32_t(127);
+        if (s.buf_bytes == 0) s.buf_bytes = 128;
+        return s;
+    }
+};
+
+#define HEPACC_CHECK(cond, ...) \
+    do {                        \
+        if (!(cond)) return fail(HEPACC_ERR_INVALID_ARG, __VA_ARGS__); \
+    } while (0)
+
+// Calls f(tag) with tag's ::type set to the C++ type of dtype t.
+template <typename T> struct Tag { using type = T; };
+
+template <typename F>
+hepacc_status with_float_type(hepacc_dtype t, F&& f) {
+    switch (t) {
+        case HEPACC_F32: return f(Tag<float>{});
+        case HEPACC_F16: return f(Tag<__half>{});
+        case HEPACC_BF16: return f(Tag<__nv_bfloat16>{});
+        default: return fail(HEPACC_ERR_DTYPE, "expected a floating content type (F32, F16, BF16)");
+    }
+}
+
+template <typename F>
+hepacc_status with_value_type(hepacc_dtype t, F&& f) {
+    switch (t) {
+        case HEPACC_F32: return f(Tag<float>{});
+        case HEPACC_F16: return f(Tag<__half>{});
+        case HEPACC_BF16: return f(Tag<__nv_bfloat16>{});
+        case HEPACC_U8: return f(Tag<uint8_t>{});
+        case HEPACC_I8: return f(Tag<int8_t>{});
+        case HEPACC_I32: return f(Tag<int32_t>{});
+        default: return fail(HEPACC_ERR_DTYPE, "unsupported content type");
+    }
+}
+
+template <typename F>
+hepacc_status with_offsets_type(hepacc_dtype t, F&& f) {
+    switch (t) {
+        case HEPACC_I32: return f(Tag<int32_t>{});
+        case HEPACC_I64: return f(Tag<int64_t>{});
+        default: return fail(HEPACC_ERR_DTYPE, "offsets must be I32 or I64");
+    }
+}
+
+template <typename K, typename... Args>
+hepacc_status launch_tiles(K kernel, const Spec& spec, int64_t n, cudaStream_t stream, Args... args) {
+    const size_t smem = static_cast<size_t>(stage_bytes_per_warp(spec)) * (kBlock / 32);
+    int grid = 0;
+    hepacc_status st = tile_grid(kernel, smem, (n + kTile - 1) / kTile, &grid);
+    if (st != HEPACC_OK) return st;
+    kernel<<<grid, kBlock, smem, stream>>>(spec, args...);
+    HEPACC_CHECK_LAUNCH("kernel launch");
+    return HEPACC_OK;
+}
+
+}  // namespace
+}  // namespace hepacc
+
+using namespace hepacc;
+
+extern "C" {
+
+hepacc_status hepacc_sum_in_offsets(const void* content, hepacc_dtype ct, const void* offsets, hepacc_dtype ot,
+                                    int64_t n, const uint8_t* mask_rows, const uint8_t* mask_content, void* out,
+                                    hepacc_dtype out_t, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(content && offsets && out, "content, offsets and out are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        const O* off = static_cast<const O*>(offsets);
+        SpecBuilder b;
+        if (is_float_type(ct)) {
+            if (out_t != HEPACC_F32) return fail(HEPACC_ERR_DTYPE, "floating content sums into F32");
+            return with_float_type(ct, [&](auto t) -> hepacc_status {
+                using T = typename decltype(t)::type;
+                b.add(content, sizeof(T), 0);
+                b.add(mask_content, 1, 0);
+                return launch_tiles(k_sum<T, O, float>, b.done(), n, s, off, n, mask_rows, static_cast<float*>(out));
+            });
+        }
+        auto run_int = [&](auto t) -> hepacc_status {
+            using T = typename decltype(t)::type;
+            b.add(content, sizeof(T), 0);
+            b.add(mask_content, 1, 0);
+            if (out_t == HEPACC_I64)
+                return launch_tiles(k_sum<T, O, int64_t>, b.done(), n, s, off, n, mask_rows, static_cast<int64_t*>(out));
+            if (out_t == HEPACC_I32 && ct != HEPACC_I64)
+                return launch_tiles(k_sum<T, O, int32_t>, b.done(), n, s, off, n, mask_rows, static_cast<int32_t*>(out));
+            return fail(HEPACC_ERR_DTYPE, "integer content sums into I32 or I64 (I64 content: I64)");
+        };
+        switch (ct) {
+            case HEPACC_U8: return run_int(Tag<uint8_t>{});
+            case HEPACC_I8: return run_int(Tag<int8_t>{});
+            case HEPACC_I32: return run_int(Tag<int32_t>{});
+            case HEPACC_I64: return run_int(Tag<int64_t>{});
+            default: return fail(HEPACC_ERR_DTYPE, "unsupported content type");
+        }
+    });
+}
+
+static hepacc_status minmax_impl(bool is_max, const void* content, hepacc_dtype ct, const void* offsets,
+                                 hepacc_dtype ot, int64_t n, const uint8_t* mask_rows, const uint8_t* mask_content,
+                                 float empty, float* out, int32_t* arg, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(content && offsets && (out || arg), "content, offsets and an output are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        return with_value_type(ct, [&](auto t) -> hepacc_status {
+            using T = typename decltype(t)::type;
+            SpecBuilder b;
+            b.add(content, sizeof(T), 0);
+            b.add(mask_content, 1, 0);
+            if (is_max)
+                return launch_tiles(k_minmax<T, O, true>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows,
+                                    empty, out, arg);
+            return launch_tiles(k_minmax<T, O, false>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows,
+                                empty, out, arg);
+        });
+    });
+}
+
+hepacc_status hepacc_max_in_offsets(const void* content, hepacc_dtype ct, const void* offsets, hepacc_dtype ot,
+                                    int64_t n, const uint8_t* mask_rows, const uint8_t* mask_content, float empty,
+                                    float* out, int32_t* arg, hepacc_stream stream) {
+    return minmax_impl(true, content, ct, offsets, ot, n, mask_rows, mask_content, empty, out, arg, stream);
+}
+
+hepacc_status hepacc_min_in_offsets(const void* content, hepacc_dtype ct, const void* offsets, hepacc_dtype ot,
+                                    int64_t n, const uint8_t* mask_rows, const uint8_t* mask_content, float empty,
+                                    float* out, int32_t* arg, hepacc_stream stream) {
+    return minmax_impl(false, content, ct, offsets, ot, n, mask_rows, mask_content, empty, out, arg, stream);
+}
+
+hepacc_status hepacc_get_in_offsets(const void* content, hepacc_dtype ct, const void* offsets, hepacc_dtype ot,
+                                    int64_t n, const int32_t* nth, int32_t nth_scalar, const uint8_t* mask_rows,
+                                    const uint8_t* mask_content, float dflt, float* out, int32_t* oidx,
+                                    hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(content && offsets && (out || oidx), "content, offsets and an output are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        return with_value_type(ct, [&](auto t) -> hepacc_status {
+            using T = typename decltype(t)::type;
+            SpecBuilder b;
+            b.add(content, sizeof(T), 0);
+            b.add(mask_content, 1, 0);
+            return launch_tiles(k_get<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, nth, nth_scalar,
+                                mask_rows, dflt, out, oidx);
+        });
+    });
+}
+
+hepacc_status hepacc_set_in_offsets(void* content, hepacc_dtype ct, const void* offsets, hepacc_dtype ot, int64_t n,
+                                    const int32_t* nth, int32_t nth_scalar, const uint8_t* mask_rows,
+                                    const uint8_t* mask_content, double value, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(content && offsets, "content and offsets are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        const O* off = static_cast<const O*>(offsets);
+        if (ct == HEPACC_U8) {
+            k_set<uint8_t, O><<<flat_grid(n), kBlock, 0, s>>>(static_cast<uint8_t*>(content), off, n, nth, nth_scalar,
+                                                              mask_rows, mask_content, static_cast<uint8_t>(value));
+        } else if (ct == HEPACC_F32) {
+            k_set<float, O><<<flat_grid(n), kBlock, 0, s>>>(static_cast<float*>(content), off, n, nth, nth_scalar,
+                                                            mask_rows, mask_content, static_cast<float>(value));
+        } else {
+            return fail(HEPACC_ERR_DTYPE, "set_in_offsets content must be U8 or F32");
+        }
+        HEPACC_CHECK_LAUNCH("set_in_offsets launch");
+        return HEPACC_OK;
+    });
+}
+
+hepacc_status hepacc_select_range(const void* content, hepacc_dtype ct, int64_t n, float scale, float lo, float hi,
+                                  int use_abs, const uint8_t* mask_in, uint8_t* mask_out, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(content && mask_out, "content and mask_out are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_value_type(ct, [&](auto t) -> hepacc_status {
+        using T = typename decltype(t)::type;
+        k_select<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, lo, hi, use_abs, mask_in,
+                                                    mask_out);
+        HEPACC_CHECK_LAUNCH("select_range launch");
+        return HEPACC_OK;
+    });
+}
+
+hepacc_status hepacc_scale(const void* content, hepacc_dtype ct, int64_t n, float scale, float* out,
+                           hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(content && out, "content and out are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_float_type(ct, [&](auto t) -> hepacc_status {
+        using T = typename decltype(t)::type;
+        k_scale<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, out);
+        HEPACC_CHECK_LAUNCH("scale launch");
+        return HEPACC_OK;
+    });
+}
+
+hepacc_status hepacc_mask_deltar(const void* eta1, const void* phi1, hepacc_dtype t1, const void* off1,
+                                 const void* eta2, const void* phi2, hepacc_dtype t2, const void* off2,
+                                 hepacc_dtype ot, int64_t n, const uint8_t* mask_rows, const uint8_t* mask1_in,
+                                 const uint8_t* mask2, float dr2_cut, uint8_t* mask1_out, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(eta1 && phi1 && off1 && eta2 && phi2 && off2 && mask1_out, "missing required pointer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        return with_float_type(t1, [&](auto a) -> hepacc_status {
+            using T1 = typename decltype(a)::type;
+            return with_float_type(t2, [&](auto b2) -> hepacc_status {
+                using T2 = typename decltype(b2)::type;
+                SpecBuilder b;
+                b.add(eta1, sizeof(T1), 0);
+                b.add(phi1, sizeof(T1), 0);
+                b.add(mask1_in, 1, 0);
+                b.add(eta2, sizeof(T2), 1, 256);
+                b.add(phi2, sizeof(T2), 1, 256);
+                b.add(mask2, 1, 1, 256);
+                return launch_tiles(k_deltar<T1, T2, O>, b.done(), n, s, static_cast<const O*>(off1),
+                                    static_cast<const O*>(off2), n, mask_rows, dr2_cut, mask1_out);
+            });
+        });
+    });
+}
+
+hepacc_status hepacc_pair_mass(const void* pt, const void* eta, const void* phi, const void* mass, hepacc_dtype t,
+                               const void* offsets, hepacc_dtype ot, int64_t n, const int32_t* ia, const int32_t* ib,
+                               const uint8_t* mask_rows, float* out, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(pt && eta && phi && mass && offsets && ia && ib && out, "missing required pointer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        return with_float_type(t, [&](auto tt) -> hepacc_status {
+            using T = typename decltype(tt)::type;
+            k_pair_mass<T, O><<<flat_grid(n), kBlock, 0, s>>>(
+                static_cast<const T*>(pt), static_cast<const T*>(eta), static_cast<const T*>(phi),
+                static_cast<const T*>(mass), static_cast<const O*>(offsets), n, ia, ib, mask_rows, out);
+            HEPACC_CHECK_LAUNCH("pair_mass launch");
+            return HEPACC_OK;
+        });
+    });
+}
+
+hepacc_status hepacc_max_pt_trijet(const void* pt, const void* eta, const void* phi, const void* mass,
+                                   hepacc_dtype t, const void* offsets, hepacc_dtype ot, int64_t n,
+                                   const uint8_t* mask_rows, const uint8_t* mask_content, float* out_mass,
+                                   float* out_pt, int32_t* out_idx3, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(pt && eta && phi && mass && offsets, "missing required pointer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        return with_float_type(t, [&](auto tt) -> hepacc_status {
+            using T = typename decltype(tt)::type;
+            SpecBuilder b;
+            b.add(pt, sizeof(T), 0);
+            b.add(eta, sizeof(T), 0);
+            b.add(phi, sizeof(T), 0);
+            b.add(mass, sizeof(T), 0);
+            b.add(mask_content, 1, 0);
+            return launch_tiles(k_trijet<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows, out_mass,
+                                out_pt, out_idx3);
+        });
+    });
+}
+
+hepacc_status hepacc_fill_histogram(const void* data, hepacc_dtype dt, const float* weights, const uint8_t* mask,
+                                    int64_t n, const float* edges, int32_t nbins, uint64_t* counts, double* sumw,
+                                    double* sumw2, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n < 0");
+    HEPACC_CHECK(nbins >= 1 && nbins <= 65536, "nbins must be in [1, 65536]");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(data && edges && counts, "data, edges and counts are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+    return with_value_type(dt, [&](auto t) -> hepacc_status {
+        using T = typename decltype(t)::type;
+        const int nbin = nbins + 2;
+        const size_t smem = static_cast<size_t>(nbin) * (8 + 8 + 4) + static_cast<size_t>(nbins + 1) * 4 + kBlock * 8;
+        if (nbin <= 4096) {
+            int grid = 0;
+            hepacc_status st = tile_grid(k_hist_smem<T>, smem, (n + 31) / 32, &grid);
+            if (st != HEPACC_OK) return st;
+            k_hist_smem<T><<<grid, kBlock, smem, s>>>(static_cast<const T*>(data), weights, mask, n, edges, nbins,
+                                                      c, sumw, sumw2);
+        } else {
+            k_hist_global<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(data), weights, mask, n, edges,
+                                                             nbins, c, sumw, sumw2);
+        }
+        HEPACC_CHECK_LAUNCH("fill_histogram launch");
+        return HEPACC_OK;
+    });
+}
+
+hepacc_status hepacc_validate_offsets(const void* offsets, hepacc_dtype ot, int64_t n, int64_t content_len,
+                                      int64_t* first_bad, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0 && content_len >= 0, "negative size");
+    HEPACC_CHECK(offsets && first_bad, "offsets and first_bad are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* fb = reinterpret_cast<unsigned long long*>(first_bad);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        k_validate_init<<<1, 1, 0, s>>>(offsets, ot == HEPACC_I64, fb);
+        if (n > 0) k_validate<O><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const O*>(offsets), n, content_len, fb);
+        k_validate_fini<<<1, 1, 0, s>>>(fb);
+        HEPACC_CHECK_LAUNCH("validate_offsets launch");
+        return HEPACC_OK;
+    });
+}
+
+}  // extern "C"
