@@ -240,6 +240,9 @@ typedef struct {
     const float *el_iso;
     const uint8_t *el_tight;
     const float *weight;
+    /* Mean jets and leptons (muons plus electrons) per event, used only to
+     * size the shared-memory staging; 0 selects 6 and 1.5. */
+    float jets_per_event, leptons_per_event;
 } hepacc_event_batch;
 
 /* Cuts, jet-pt scale variations and the 20 histograms. HOST memory: the call

@@ -1,0 +1,937 @@
+// The fused benchmark chain of Section IV of arXiv:1906.06242: kernel
+// templates shared by the per-type translation units (chain_f32.cu,
+// chain_bf16.cu, chain_f16.cu) and the host entry point (chain.cu).
+//
+// One kernel, persistent blocks; a block works on tiles of E = blockDim.x
+// consecutive events (thread = event):
+//  * staging: thread 0 copies every needed column's span of the tile into
+//    one of two shared-memory stage buffers with bulk asynchronous copies
+//    (cp.async.bulk, the TMA engine; whole 16-byte chunks), completion on a
+//    "full" mbarrier; warps release a stage on an "empty" mbarrier, so they
+//    run independently (up to one tile apart) without block barriers; the
+//    tile spans are read two tiles ahead;
+//  * selection (thread = event, staged data): lepton selection, jet
+//    acceptance (|eta|, Delta R to the selected leptons), per jet-pt
+//    variation the jet counts that decide the event; for a passing event
+//    the same thread then gathers HT, the mass sum, the leading jets and the
+//    max-|sum pT| triplet (ranked in registers) from shared memory and
+//    queues the (event, variation) with the jets' four-momenta in a per-warp
+//    queue;
+//  * masses (thread = queued pair, 32 at a time per warp): pair and triplet
+//    invariant masses and the 20 variables, pure arithmetic;
+//  * fill: per histogram, lanes bin the warp's queued values, lanes that hit
+//    the same bin are merged, one shared-memory atomic per bin (or a global
+//    one when n_var histogram copies do not fit in shared memory); blocks
+//    add their histograms to the output at exit.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "hepacc_host.h"
+#include "hepacc_tiles.cuh"
+
+namespace hepacc {
+namespace chain {
+
+constexpr int NC = 15;            // staged columns
+constexpr int kNV = HEPACC_CHAIN_NVARS;
+constexpr int kQ = kNV + 1;       // fill entry: 20 variables + variation
+constexpr int kScratch = 10;      // selected jets ranked from a queue slot (2 x 10 words of it)
+constexpr int kMaxThreads = 384;
+constexpr int kHdr = 96;          // stage header: spans, staged flag, column offsets
+
+enum : int { J_PT = 0, J_ETA, J_PHI, J_MASS, J_BTAG, M_PT, M_ETA, M_PHI, M_ISO, M_TIGHT, E_PT, E_ETA, E_PHI, E_ISO, E_TIGHT };
+
+struct ChainParams {
+    float lep_pt_min, lep_abseta_max, lep_iso_max;
+    float jet_pt_min, jet_abseta_max, dr2_cut, btag_min;
+    int n_var;
+    int total_bins;
+    int n_edges;
+    float scales[HEPACC_MAX_VARIATIONS];
+    int nbins[kNV];
+    int eoff[kNV];      // first edge of histogram h
+    int boff[kNV];      // first bin of histogram h inside a variation block
+    float edges[HEPACC_CHAIN_MAX_EDGES];
+};
+
+struct ChainOut {
+    unsigned long long* counts;
+    double* sumw;
+    double* sumw2;
+    uint8_t* ev_pass;
+    int32_t* ev_nlep;
+    int32_t* ev_njet;
+    int32_t* ev_nb;
+    int32_t* ev_idx;
+    float* ev_vars;
+};
+
+struct ChainCols {
+    const void *jet_pt, *jet_eta, *jet_phi, *jet_mass, *jet_btag;
+    const void *mu_pt, *mu_eta, *mu_phi;
+    const float *mu_iso;
+    const uint8_t *mu_tight;
+    const void *el_pt, *el_eta, *el_phi;
+    const float *el_iso;
+    const uint8_t *el_tight;
+    const float *weight;
+};
+
+// Shared-memory layout of a block (byte offsets into dynamic shared memory).
+struct Layout {
+    ColSpec col[NC];       // soff relative to the stage's column area
+    uint32_t stage_bytes;  // one stage: kHdr header + column regions
+    uint32_t bars;         // four mbarriers: full[2], empty[2]
+    uint32_t edges;        // n_edges floats
+    uint32_t queue;        // per warp 32 slots of R_WORDS words
+    uint32_t acc;          // per warp acc_words words of jet acceptance flags
+    int acc_words;
+    uint32_t tri;          // triplet table (uint16 per triplet, colex order)
+    uint32_t hist;         // block-private histograms (SMEM_HIST)
+    uint32_t total;
+};
+
+// A queued (event, variation): words of a per-warp queue slot. Jets are
+// (pt_k, eta, phi, mass); the leading one also carries btag.
+enum : int {
+    R_E = 0, R_K, R_NJ, R_IDX, R_TAB, R_TC, R_HT, R_SUMM, R_MAXBT, R_BEST, R_W,
+    R_LPT, R_LETA, R_LPHI, R_LISO,
+    R_J1 = 15, R_J2 = 20, R_T1 = 24, R_T2 = 28, R_T3 = 32, R_WORDS = 36
+};
+
+__device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
+
+template <typename T>
+__device__ __forceinline__ float gload(const void* p, int64_t i) {
+    return Elem<T>::f(static_cast<const T*>(p)[i]);
+}
+
+// Jet acceptance straight from global memory (|eta| and Delta R to every
+// selected lepton of event e); used for jets past the 64 cached flags.
+template <typename KT, typename OffT>
+__device__ bool jet_ok_global(const ChainParams& P, const ChainCols& C, const OffT* moff, const OffT* eoff,
+                              int64_t e, int64_t i) {
+    const float eta = gload<KT>(C.jet_eta, i);
+    if (!(fabsf(eta) < P.jet_abseta_max)) return false;
+    const float phi = gload<KT>(C.jet_phi, i);
+    for (int f = 0; f < 2; ++f) {
+        const OffT* off = f == 0 ? moff : eoff;
+        const void* pt = f == 0 ? C.mu_pt : C.el_pt;
+        const void* le = f == 0 ? C.mu_eta : C.el_eta;
+        const void* lp = f == 0 ? C.mu_phi : C.el_phi;
+        const float* iso = f == 0 ? C.mu_iso : C.el_iso;
+        const uint8_t* tight = f == 0 ? C.mu_tight : C.el_tight;
+        for (int64_t l = ldoff(off, e); l < ldoff(off, e + 1); ++l) {
+            const float p = gload<KT>(pt, l), x = gload<KT>(le, l);
+            const bool sel = p > P.lep_pt_min && fabsf(x) < P.lep_abseta_max && tight[l] != 0 && iso[l] < P.lep_iso_max;
+            if (sel && dr2_f32(eta, phi, x, gload<KT>(lp, l)) < P.dr2_cut) return false;
+        }
+    }
+    return true;
+}
+
+// Column access for the selection phase.
+struct StagedCols {
+    uint32_t off[NC];      // byte offset of the tile's first element of each column in shared memory
+    template <typename T>
+    __device__ __forceinline__ T ld(int c, int r) const {
+        return *reinterpret_cast<const T*>(g_dyn_smem + off[c] + r * static_cast<int>(sizeof(T)));
+    }
+};
+struct DirectCols {
+    const Layout* L;       // column bases (kernel parameters)
+    int64_t S[3];          // the tile's first element per collection
+    template <typename T>
+    __device__ __forceinline__ T ld(int c, int r) const {
+        return reinterpret_cast<const T*>(L->col[c].base)[S[L->col[c].coll] + r];
+    }
+};
+
+__device__ __forceinline__ void put4(uint32_t* q, float a, float b, float c, float d) {
+    q[0] = __float_as_uint(a);
+    q[1] = __float_as_uint(b);
+    q[2] = __float_as_uint(c);
+    q[3] = __float_as_uint(d);
+}
+
+template <typename KT, typename BT, typename OffT, bool DEBUG, bool SMEM_HIST>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant__ Layout L,
+                                                          const __grid_constant__ ChainParams P, ChainCols C,
+                                                          const OffT* joff, const OffT* moff, const OffT* eoff,
+                                                          int64_t n, ChainOut out) {
+    unsigned char* smem = g_dyn_smem;
+    const int tid = threadIdx.x;
+    const int E = blockDim.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nwarp = E >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    float* s_edges = reinterpret_cast<float*>(smem + L.edges);
+    uint32_t* my_q = reinterpret_cast<uint32_t*>(smem + L.queue) + warp * 32 * R_WORDS;
+    const int hist_n = P.n_var * P.total_bins;
+    double* s_w = reinterpret_cast<double*>(smem + L.hist);
+    double* s_w2 = s_w + (SMEM_HIST ? hist_n : 0);
+    unsigned int* s_c = reinterpret_cast<unsigned int*>(s_w2 + (SMEM_HIST ? hist_n : 0));
+    uint16_t* s_tri = reinterpret_cast<uint16_t*>(smem + L.tri);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+    const uint32_t full[2] = {smem_addr(bars), smem_addr(bars + 1)};
+    const uint32_t empty[2] = {smem_addr(bars + 2), smem_addr(bars + 3)};
+    const uint32_t smem0 = smem_addr(smem);
+
+    for (int i = tid; i < P.n_edges; i += E) s_edges[i] = P.edges[i];
+    // all triplets a<b<c<kScratch in colex order (c, then b, then a): the
+    // first C(n,3) are those among n jets
+    if (tid == 0) {
+        int t = 0;
+        for (int c = 2; c < kScratch; ++c)
+            for (int b2 = 1; b2 < c; ++b2)
+                for (int a = 0; a < b2; ++a) s_tri[t++] = static_cast<uint16_t>(a | (b2 << 4) | (c << 8));
+    }
+    if (SMEM_HIST) {
+        for (int i = tid; i < hist_n; i += E) {
+            s_w[i] = 0.0;
+            s_w2[i] = 0.0;
+            s_c[i] = 0u;
+        }
+    }
+    if (tid == 0) {
+        mbar_init(full[0], 1);
+        mbar_init(full[1], 1);
+        mbar_init(empty[0], nwarp);
+        mbar_init(empty[1], nwarp);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const OffT* const offs[3] = {joff, moff, eoff};
+    const int64_t ntiles = (n + E - 1) / E;
+    const int64_t grid = gridDim.x;
+
+    // thread 0: first and last element of every collection in tile tt
+    auto load_span = [&](int64_t tt, int64_t (&S)[3], int64_t (&T)[3]) {
+        const int64_t a = tt * E;
+        const int64_t z = a + E < n ? a + E : n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            S[c] = ldoff(offs[c], a);
+            T[c] = ldoff(offs[c], z);
+        }
+    };
+    // thread 0: header of stage b and the bulk copies of the tile's spans
+    auto issue = [&](int b, const int64_t (&S)[3], const int64_t (&T)[3]) {
+        unsigned char* st = smem + b * L.stage_bytes;
+        int64_t* hdr = reinterpret_cast<int64_t*>(st);
+        uint32_t* hoff = reinterpret_cast<uint32_t*>(st + 32);
+        bool fits = true;
+        uint32_t total = 0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const ColSpec& cs = L.col[c];
+            const uintptr_t a = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
+            const uintptr_t z = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
+            const uintptr_t bytes = T[cs.coll] > S[cs.coll] ? ((z + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)) : 0;
+            if (bytes > cs.cap) fits = false;
+            total += static_cast<uint32_t>(bytes);
+            hoff[c] = b * L.stage_bytes + kHdr + cs.soff + static_cast<uint32_t>(a & 15u);
+        }
+        hdr[0] = S[0];
+        hdr[1] = S[1];
+        hdr[2] = S[2];
+        hoff[NC] = fits ? 1u : 0u;
+        fence_proxy_async_smem();
+        if (fits) {
+            mbar_arrive_expect_tx(full[b], total);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const ColSpec& cs = L.col[c];
+                if (T[cs.coll] <= S[cs.coll]) continue;
+                const uintptr_t a = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
+                const uintptr_t z = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
+                const uintptr_t a16 = a & ~uintptr_t(15);
+                const uint32_t bytes = static_cast<uint32_t>(((z + 15) & ~uintptr_t(15)) - a16);
+                bulk_g2s(smem0 + b * L.stage_bytes + kHdr + cs.soff, reinterpret_cast<const void*>(a16), bytes, full[b]);
+            }
+        } else {
+            mbar_arrive_expect_tx(full[b], 0);
+        }
+    };
+
+    // Masses and fill for this warp's queued records [0, m) (warp-uniform).
+    auto flush = [&](int m) {
+        const uint32_t* r = my_q + lane * R_WORDS;   // this lane's record
+        const bool have = lane < m;
+        float var[kNV];
+        int k = 0;
+        bool pass = false;
+        if (have) {
+            k = r[R_K] & 0xff;
+            pass = ((r[R_K] >> 8) & 1u) != 0;
+            const int nlep = r[R_K] >> 16;
+            const int njet = r[R_NJ] & 0xffff;
+            const int lead = static_cast<int16_t>(r[R_IDX] & 0xffff), sub = static_cast<int16_t>(r[R_IDX] >> 16);
+            const int ta = static_cast<int16_t>(r[R_TAB] & 0xffff), tb = static_cast<int16_t>(r[R_TAB] >> 16);
+            const int tc = static_cast<int32_t>(r[R_TC]);
+            auto f = [&](int w) { return __uint_as_float(r[w]); };
+#pragma unroll
+            for (int h = 0; h < kNV; ++h) var[h] = qnan();
+            var[0] = f(R_HT);
+            var[8] = static_cast<float>(njet);
+            var[9] = static_cast<float>(r[R_NJ] >> 16);
+            var[10] = f(R_MAXBT);
+            var[18] = f(R_SUMM);
+            var[19] = f(R_W);
+            if (nlep >= 1) {
+                var[13] = f(R_LPT);
+                var[14] = f(R_LETA);
+                var[15] = f(R_LPHI);
+                var[16] = f(R_LISO);
+                var[17] = __fadd_rn(var[0], var[13]);
+            }
+            MassObj ol, os;
+            if (lead >= 0) {
+                var[1] = f(R_J1);
+                var[2] = f(R_J1 + 1);
+                var[3] = f(R_J1 + 2);
+                var[4] = f(R_J1 + 3);
+                var[5] = f(R_J1 + 4);
+                ol = mass_obj(var[1], var[2], var[3], var[4]);
+            }
+            if (sub >= 0) {
+                var[6] = f(R_J2);
+                os = mass_obj(var[6], f(R_J2 + 1), f(R_J2 + 2), f(R_J2 + 3));
+                var[7] = mass2obj(ol, os);
+            }
+            if (njet >= 3) {
+                // the triplet's four-momenta; jets shared with the leading pair reuse its terms
+                auto obj = [&](int idx, int w) {
+                    if (idx == lead) return ol;
+                    if (idx == sub) return os;
+                    return mass_obj(f(w), f(w + 1), f(w + 2), f(w + 3));
+                };
+                const MassObj oa = obj(ta, R_T1), ob = obj(tb, R_T2), oc = obj(tc, R_T3);
+                var[11] = mass3obj(oa, ob, oc);
+                var[12] = sqrtf(f(R_BEST));
+            }
+            if (DEBUG) {
+                const int64_t e = r[R_E];
+                const int64_t kn = static_cast<int64_t>(k) * n;
+                if (out.ev_pass) out.ev_pass[kn + e] = pass ? 1 : 0;
+                if (out.ev_njet) out.ev_njet[kn + e] = njet;
+                if (out.ev_nb) out.ev_nb[kn + e] = static_cast<int32_t>(r[R_NJ] >> 16);
+                if (out.ev_idx) {
+                    int32_t* ix = out.ev_idx + static_cast<int64_t>(k) * 5 * n;
+                    ix[e] = lead;
+                    ix[n + e] = sub;
+                    ix[2 * n + e] = njet >= 3 ? ta : -1;
+                    ix[3 * n + e] = njet >= 3 ? tb : -1;
+                    ix[4 * n + e] = njet >= 3 ? tc : -1;
+                }
+                if (out.ev_vars) {
+                    float* vv = out.ev_vars + static_cast<int64_t>(k) * kNV * n;
+#pragma unroll
+                    for (int h = 0; h < kNV; ++h) vv[h * n + e] = var[h];
+                }
+            }
+        }
+        __syncwarp();
+        // fill entries overwrite the records: 20 variables and the variation
+        // (0xffffffff: nothing to fill)
+        if (have) {
+            uint32_t* q = my_q + lane * R_WORDS;
+#pragma unroll
+            for (int h = 0; h < kNV; ++h) q[h] = __float_as_uint(var[h]);
+            q[kNV] = pass ? static_cast<uint32_t>(k) : 0xffffffffu;
+        }
+        __syncwarp();
+        // lane h fills histogram h for every queued entry (distinct lanes,
+        // distinct histograms: no two lanes of the warp touch the same bin)
+        if (lane < kNV) {
+            const int h = lane;
+            const float* eh = s_edges + P.eoff[h];
+            const int nb_h = P.nbins[h];
+            const float span = eh[nb_h] - eh[0];
+            const float invw = span > 0.0f ? static_cast<float>(nb_h) / span : 0.0f;
+            const int boff = P.boff[h];
+            for (int j = 0; j < m; ++j) {
+                const uint32_t* q = my_q + j * R_WORDS;
+                const uint32_t kk = q[kNV];
+                if (kk == 0xffffffffu) continue;
+                const int bin = find_bin(__uint_as_float(q[h]), eh, nb_h, invw);
+                if (bin < 0) continue;
+                const int at = static_cast<int>(kk) * P.total_bins + boff + bin;
+                const double wd = static_cast<double>(__uint_as_float(q[19]));
+                if (SMEM_HIST) {
+                    atomicAdd(&s_c[at], 1u);
+                    atomicAdd(&s_w[at], wd);
+                    if (out.sumw2) atomicAdd(&s_w2[at], wd * wd);
+                } else {
+                    atomicAdd(&out.counts[at], 1ull);
+                    atomicAdd(&out.sumw[at], wd);
+                    if (out.sumw2) atomicAdd(&out.sumw2[at], wd * wd);
+                }
+            }
+        }
+        __syncwarp();
+    };
+
+    int qcount = 0;
+    int64_t tile = blockIdx.x;
+    int64_t (&S1)[3] = *reinterpret_cast<int64_t(*)[3]>(smem + L.bars + 32);   // thread 0: spans of the next tile
+    int64_t (&T1)[3] = *reinterpret_cast<int64_t(*)[3]>(smem + L.bars + 56);
+    int64_t cs_[3] = {0, 0, 0}, ct_[3] = {0, 0, 0};
+    uint32_t fpar[2] = {0u, 0u};
+    uint32_t uses[2] = {0u, 0u};   // thread 0: copies issued into each stage
+    int b = 0;
+    if (tile < ntiles) {
+        if (tid == 0) {
+            int64_t S0[3], T0[3];
+            load_span(tile, S0, T0);
+            issue(0, S0, T0);
+            uses[0] = 1;
+            if (tile + grid < ntiles) load_span(tile + grid, S1, T1);
+        }
+        const int64_t e = tile * E + tid;
+        const int64_t elo = e < n ? e : n, ehi = e + 1 < n ? e + 1 : n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cs_[c] = ldoff(offs[c], elo);
+            ct_[c] = ldoff(offs[c], ehi);
+        }
+    }
+    for (; tile < ntiles; tile += grid) {
+        const int64_t next = tile + grid;
+        if (tid == 0 && next < ntiles) {
+            // the other stage is free once every warp released its previous tile
+            bool ok = true;
+            if (uses[b ^ 1] > 0) ok = mbar_wait_bounded(empty[b ^ 1], (uses[b ^ 1] - 1) & 1u);
+            if (ok) {
+                issue(b ^ 1, S1, T1);
+                ++uses[b ^ 1];
+                if (next + grid < ntiles) load_span(next + grid, S1, T1);
+            }
+        }
+        __syncwarp();
+        int64_t ns_[3] = {0, 0, 0}, nt_[3] = {0, 0, 0};
+        if (next < ntiles) {
+            const int64_t e = next * E + tid;
+            const int64_t elo = e < n ? e : n, ehi = e + 1 < n ? e + 1 : n;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ns_[c] = ldoff(offs[c], elo);
+                nt_[c] = ldoff(offs[c], ehi);
+            }
+        }
+        if (!mbar_wait_bounded(full[b], fpar[b])) break;   // error word set; this warp stops
+        fpar[b] ^= 1u;
+
+        const unsigned char* st = smem + b * L.stage_bytes;
+        const int64_t* hdr = reinterpret_cast<const int64_t*>(st);
+        const uint32_t* hoff = reinterpret_cast<const uint32_t*>(st + 32);
+        const int64_t e = tile * E + tid;
+        const bool valid = e < n;
+        int rs[3], rt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rs[c] = static_cast<int>(cs_[c] - hdr[c]);
+            rt[c] = static_cast<int>(ct_[c] - hdr[c]);
+        }
+        const bool staged = hoff[NC] != 0;
+        StagedCols sc;
+        DirectCols dc;
+        dc.L = &L;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dc.S[c] = hdr[c];
+        if (staged) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) sc.off[c] = hoff[c];
+        }
+
+        // this warp's spans per collection (tile-relative)
+        int W0[3], W1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            W0[c] = __shfl_sync(0xffffffffu, rs[c], 0);
+            W1[c] = __shfl_sync(0xffffffffu, rt[c], 31);
+        }
+        // bits of [lo, hi) inside the 32-element window starting at base
+        auto range_mask = [](int lo, int hi, int base) -> unsigned {
+            const int a = lo - base > 0 ? lo - base : 0;
+            const int z = hi - base < 32 ? hi - base : 32;
+            if (z <= a) return 0u;
+            const unsigned top = z >= 32 ? 0xffffffffu : ((1u << z) - 1u);
+            return top & ~((1u << a) - 1u);
+        };
+        auto lep_sel = [&](const auto& T, int c0, int i) -> bool {
+            return Elem<KT>::f(T.template ld<KT>(c0, i)) > P.lep_pt_min &&
+                   fabsf(Elem<KT>::f(T.template ld<KT>(c0 + 1, i))) < P.lep_abseta_max &&
+                   T.template ld<uint8_t>(c0 + 4, i) != 0 && T.template ld<float>(c0 + 3, i) < P.lep_iso_max;
+        };
+
+        // selection, lanes over objects: leptons (muons first, then
+        // electrons); per event the count and the first selected one
+        int nlep = 0, lfirst = -1, lflav = 0;
+        auto leptons = [&](const auto& T) {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const int c0 = f == 0 ? M_PT : E_PT;
+                const int coll = 1 + f;
+                for (int base = W0[coll]; base < W1[coll]; base += 32) {
+                    const int p = base + lane;
+                    const bool sel = p < W1[coll] && lep_sel(T, c0, p);
+                    const unsigned hit = __ballot_sync(0xffffffffu, sel) & range_mask(rs[coll], rt[coll], base);
+                    nlep += __popc(hit);
+                    if (lfirst < 0 && hit) {
+                        lfirst = base + __ffs(hit) - 1;
+                        lflav = f;
+                    }
+                }
+            }
+        };
+        if (staged)
+            leptons(sc);
+        else
+            leptons(dc);
+        if (!valid) nlep = 0;
+        float lpt = qnan(), leta = qnan(), lphi = qnan(), liso = qnan();
+        auto lep_vals = [&](const auto& T) {
+            if (lfirst < 0) return;
+            if (lflav == 0) {
+                lpt = Elem<KT>::f(T.template ld<KT>(M_PT, lfirst));
+                leta = Elem<KT>::f(T.template ld<KT>(M_ETA, lfirst));
+                lphi = Elem<KT>::f(T.template ld<KT>(M_PHI, lfirst));
+                liso = T.template ld<float>(M_ISO, lfirst);
+            } else {
+                lpt = Elem<KT>::f(T.template ld<KT>(E_PT, lfirst));
+                leta = Elem<KT>::f(T.template ld<KT>(E_ETA, lfirst));
+                lphi = Elem<KT>::f(T.template ld<KT>(E_PHI, lfirst));
+                liso = T.template ld<float>(E_ISO, lfirst);
+            }
+        };
+        if (valid) {
+            if (staged)
+                lep_vals(sc);
+            else
+                lep_vals(dc);
+        }
+        if (DEBUG && valid && out.ev_nlep) out.ev_nlep[e] = nlep;
+        // without per-event outputs only single-lepton events can pass
+        const bool active = valid && (DEBUG || nlep == 1);
+        const unsigned amask = __ballot_sync(0xffffffffu, active);
+
+        // jet acceptance (|eta|, Delta R >= cut to every selected lepton of
+        // the jet's event), lanes over jets; one word of flags per 32 jets
+        const int nround = (W1[0] - W0[0] + 31) >> 5;
+        const bool acc_cached = nround <= L.acc_words;
+        uint32_t* accw = reinterpret_cast<uint32_t*>(smem + L.acc) + warp * L.acc_words;
+        // Delta R test of jet (eta, phi) against every selected lepton of the
+        // event whose lepton ranges are given (events with several leptons)
+        auto far_from_all = [&](const auto& T, float eta, float phi, int m0, int m1, int e0, int e1) -> bool {
+            for (int l = m0; l < m1; ++l)
+                if (lep_sel(T, M_PT, l) && dr2_f32(eta, phi, Elem<KT>::f(T.template ld<KT>(M_ETA, l)),
+                                                   Elem<KT>::f(T.template ld<KT>(M_PHI, l))) < P.dr2_cut)
+                    return false;
+            for (int l = e0; l < e1; ++l)
+                if (lep_sel(T, E_PT, l) && dr2_f32(eta, phi, Elem<KT>::f(T.template ld<KT>(E_ETA, l)),
+                                                   Elem<KT>::f(T.template ld<KT>(E_PHI, l))) < P.dr2_cut)
+                    return false;
+            return true;
+        };
+        auto accept = [&](const auto& T) {
+            for (int r = 0; r < nround && r < L.acc_words; ++r) {
+                const int base = W0[0] + 32 * r;
+                const int p = base + lane;
+                // owner of jet p: the last lane whose jets start at or before p
+                int own = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, rs[0], own + step);
+                    if (v <= p) own += step;
+                }
+                const int kind = __shfl_sync(0xffffffffu, nlep, own);
+                const float le = __shfl_sync(0xffffffffu, leta, own);
+                const float lp = __shfl_sync(0xffffffffu, lphi, own);
+                const int m0 = __shfl_sync(0xffffffffu, rs[1], own), m1 = __shfl_sync(0xffffffffu, rt[1], own);
+                const int e0 = __shfl_sync(0xffffffffu, rs[2], own), e1 = __shfl_sync(0xffffffffu, rt[2], own);
+                bool ok = false;
+                if (p < W1[0] && ((amask >> own) & 1u)) {
+                    const float eta = Elem<KT>::f(T.template ld<KT>(J_ETA, p));
+                    if (fabsf(eta) < P.jet_abseta_max) {
+                        const float phi = Elem<KT>::f(T.template ld<KT>(J_PHI, p));
+                        if (kind == 1)
+                            ok = !(dr2_f32(eta, phi, le, lp) < P.dr2_cut);
+                        else if (kind == 0)
+                            ok = true;
+                        else
+                            ok = far_from_all(T, eta, phi, m0, m1, e0, e1);
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (lane == 0) accw[r] = m;
+            }
+        };
+        if (amask) {
+            if (staged)
+                accept(sc);
+            else
+                accept(dc);
+        }
+        __syncwarp();
+        // acceptance of jet i by its own lane (flags, or recomputed past them)
+        auto acc_of = [&](const auto& T, int i) -> bool {
+            const int q = i - W0[0];
+            if ((q >> 5) < L.acc_words) return ((accw[q >> 5] >> (q & 31)) & 1u) != 0;
+            const float eta = Elem<KT>::f(T.template ld<KT>(J_ETA, i));
+            if (!(fabsf(eta) < P.jet_abseta_max)) return false;
+            const float phi = Elem<KT>::f(T.template ld<KT>(J_PHI, i));
+            if (nlep == 1) return !(dr2_f32(eta, phi, leta, lphi) < P.dr2_cut);
+            if (nlep == 0) return true;
+            return far_from_all(T, eta, phi, rs[1], rt[1], rs[2], rt[2]);
+        };
+        auto jet_sel = [&](const auto& T, int i, float s, float& ptk) -> bool {
+            if (!acc_of(T, i)) return false;
+            ptk = __fmul_rn(Elem<KT>::f(T.template ld<KT>(J_PT, i)), s);
+            return ptk > P.jet_pt_min;
+        };
+        // per variation: jet and b-jet counts, lanes over jets
+        auto count = [&](const auto& T, float s, int& njet, int& nbj) {
+            for (int base = W0[0]; base < W1[0]; base += 32) {
+                const int p = base + lane;
+                bool sel = false, bsel = false;
+                if (p < W1[0] && acc_cached && ((accw[(base - W0[0]) >> 5] >> lane) & 1u)) {
+                    sel = __fmul_rn(Elem<KT>::f(T.template ld<KT>(J_PT, p)), s) > P.jet_pt_min;
+                    bsel = sel && Elem<BT>::f(T.template ld<BT>(J_BTAG, p)) > P.btag_min;
+                }
+                const unsigned rm = range_mask(rs[0], rt[0], base);
+                njet += __popc(__ballot_sync(0xffffffffu, sel) & rm);
+                nbj += __popc(__ballot_sync(0xffffffffu, bsel) & rm);
+            }
+            if (!acc_cached && active) {
+                // flags not cached for this tile: count this lane's jets itself
+                njet = 0;
+                nbj = 0;
+                for (int i = rs[0]; i < rt[0]; ++i) {
+                    float ptk;
+                    if (!jet_sel(T, i, s, ptk)) continue;
+                    ++njet;
+                    nbj += Elem<BT>::f(T.template ld<BT>(J_BTAG, i)) > P.btag_min ? 1 : 0;
+                }
+            }
+        };
+        // a queued event, by its own lane: HT and the mass sum (element
+        // order), leading pair, max btag; the transverse momenta and tile
+        // indices of the first kScratch selected jets go to the slot (its
+        // jet area and first words are free until the record is written)
+        auto sums = [&](const auto& T, float s, uint32_t* r, int& nsel, int& lead, int& sub) {
+            float ht = 0.0f, summ = 0.0f, maxbt = qnan(), lead_pt = 0.0f, sub_pt = 0.0f;
+            lead = -1;
+            sub = -1;
+            float* sx = reinterpret_cast<float*>(r + R_J1);
+            float* sy = sx + kScratch;
+            int16_t* li = reinterpret_cast<int16_t*>(r);
+            nsel = 0;
+            for (int i = rs[0]; i < rt[0]; ++i) {
+                float ptk;
+                if (!jet_sel(T, i, s, ptk)) continue;
+                const float bt = Elem<BT>::f(T.template ld<BT>(J_BTAG, i));
+                ht = __fadd_rn(ht, ptk);
+                summ = __fadd_rn(summ, Elem<KT>::f(T.template ld<KT>(J_MASS, i)));
+                if (lead < 0 || ptk > lead_pt) {
+                    sub = lead;
+                    sub_pt = lead_pt;
+                    lead = i;
+                    lead_pt = ptk;
+                } else if (sub < 0 || ptk > sub_pt) {
+                    sub = i;
+                    sub_pt = ptk;
+                }
+                if (!(bt != bt) && (maxbt != maxbt || bt > maxbt)) maxbt = bt;
+                if (nsel < kScratch) {
+                    float sn, cs;
+                    __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, i)), &sn, &cs);
+                    sx[nsel] = ptk * cs;
+                    sy[nsel] = ptk * sn;
+                    li[nsel] = static_cast<int16_t>(i);
+                }
+                ++nsel;
+            }
+            r[R_HT] = __float_as_uint(ht);
+            r[R_SUMM] = __float_as_uint(summ);
+            r[R_MAXBT] = __float_as_uint(maxbt);
+        };
+        // more selected jets than the scratch holds: the owning lane ranks all
+        // triplets itself from the tile
+        auto slow_triplet = [&](const auto& T, float s, float& best, int& ta, int& tb, int& tc) {
+            for (int a = rs[0]; a < rt[0]; ++a) {
+                float pa;
+                if (!jet_sel(T, a, s, pa)) continue;
+                float sa, ca;
+                __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, a)), &sa, &ca);
+                for (int bq = a + 1; bq < rt[0]; ++bq) {
+                    float pb;
+                    if (!jet_sel(T, bq, s, pb)) continue;
+                    float sb, cb;
+                    __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, bq)), &sb, &cb);
+                    const float bx = pa * ca + pb * cb, by = pa * sa + pb * sb;
+                    for (int c = bq + 1; c < rt[0]; ++c) {
+                        float pc;
+                        if (!jet_sel(T, c, s, pc)) continue;
+                        float sc2, cc;
+                        __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, c)), &sc2, &cc);
+                        const float tx = bx + pc * cc, ty = by + pc * sc2;
+                        const float val = tx * tx + ty * ty;
+                        if (val > best) {
+                            best = val;
+                            ta = a;
+                            tb = bq;
+                            tc = c;
+                        }
+                    }
+                }
+            }
+        };
+        auto jet4 = [&](const auto& T, float s, int i, uint32_t* q) {
+            put4(q, __fmul_rn(Elem<KT>::f(T.template ld<KT>(J_PT, i)), s), Elem<KT>::f(T.template ld<KT>(J_ETA, i)),
+                 Elem<KT>::f(T.template ld<KT>(J_PHI, i)), Elem<KT>::f(T.template ld<KT>(J_MASS, i)));
+        };
+
+        const float w = valid ? C.weight[e] : 0.0f;
+        for (int k = 0; k < P.n_var; ++k) {
+            const float s = P.scales[k];
+            int njet = 0, nbj = 0;
+            if (amask) {
+                if (staged)
+                    count(sc, s, njet, nbj);
+                else
+                    count(dc, s, njet, nbj);
+            }
+            if (!active) {
+                njet = 0;
+                nbj = 0;
+            }
+            const bool pass = active && nlep == 1 && njet >= 2 && nbj >= 1;
+            const bool enq = DEBUG ? valid : pass;
+            const unsigned emask = __ballot_sync(0xffffffffu, enq);
+            const int m = __popc(emask);
+            if (m == 0) continue;
+            if (qcount + m > 32) {
+                flush(qcount);
+                qcount = 0;
+            }
+            uint32_t* r = my_q + (qcount + __popc(emask & lt_mask)) * R_WORDS;
+            int nsel = 0, lead = -1, sub = -1;
+            if (enq) {
+                if (staged)
+                    sums(sc, s, r, nsel, lead, sub);
+                else
+                    sums(dc, s, r, nsel, lead, sub);
+            }
+            __syncwarp();
+            // max |sum pT| triplet of every queued event: lanes over its
+            // triplets (colex order table), largest value wins, ties go to the
+            // smallest (a, b, c), i.e. the first in lexicographic order
+            float my_best = -1.0f;
+            int my_key = -1;
+            for (unsigned em = emask; em; em &= em - 1) {
+                const int L = __ffs(em) - 1;
+                const int nL = __shfl_sync(0xffffffffu, nsel, L);
+                if (nL < 3 || nL > kScratch) continue;
+                const float* qx = reinterpret_cast<const float*>(my_q + (qcount + __popc(emask & ((1u << L) - 1u))) * R_WORDS + R_J1);
+                const float* qy = qx + kScratch;
+                const int ntri = nL * (nL - 1) * (nL - 2) / 6;
+                float bv = -1.0f;
+                int bk = 0xfff;
+                for (int t = lane; t < ntri; t += 32) {
+                    const int abc = s_tri[t];
+                    const int a = abc & 15, b2 = (abc >> 4) & 15, c = abc >> 8;
+                    const float tx = (qx[a] + qx[b2]) + qx[c], ty = (qy[a] + qy[b2]) + qy[c];
+                    const float val = tx * tx + ty * ty;
+                    const int key = (a << 8) | (b2 << 4) | c;
+                    if (val > bv || (val == bv && key < bk)) {
+                        bv = val;
+                        bk = key;
+                    }
+                }
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv, d);
+                    const int ok = __shfl_xor_sync(0xffffffffu, bk, d);
+                    if (ov > bv || (ov == bv && ok < bk)) {
+                        bv = ov;
+                        bk = ok;
+                    }
+                }
+                if (lane == L) {
+                    my_best = bv;
+                    my_key = bk;
+                }
+            }
+            if (enq) {
+                float best = -1.0f;
+                int ta = -1, tb = -1, tc = -1;
+                const int16_t* li = reinterpret_cast<const int16_t*>(r);
+                if (nsel >= 3 && nsel <= kScratch) {
+                    best = my_best;
+                    ta = li[my_key >> 8];
+                    tb = li[(my_key >> 4) & 15];
+                    tc = li[my_key & 15];
+                } else if (nsel > kScratch) {
+                    if (staged)
+                        slow_triplet(sc, s, best, ta, tb, tc);
+                    else
+                        slow_triplet(dc, s, best, ta, tb, tc);
+                }
+                r[R_BEST] = __float_as_uint(best);
+                const int l16 = lead < 0 ? 0xffff : (lead - rs[0]) & 0xffff;
+                const int s16 = sub < 0 ? 0xffff : (sub - rs[0]) & 0xffff;
+                r[R_IDX] = static_cast<uint32_t>(l16) | (static_cast<uint32_t>(s16) << 16);
+                const int a16 = ta < 0 ? 0xffff : (ta - rs[0]) & 0xffff;
+                const int b16 = tb < 0 ? 0xffff : (tb - rs[0]) & 0xffff;
+                r[R_TAB] = static_cast<uint32_t>(a16) | (static_cast<uint32_t>(b16) << 16);
+                r[R_TC] = static_cast<uint32_t>(tc < 0 ? -1 : tc - rs[0]);
+                auto write4 = [&](const auto& T) {
+                    if (lead >= 0) {
+                        jet4(T, s, lead, r + R_J1);
+                        r[R_J1 + 4] = __float_as_uint(Elem<BT>::f(T.template ld<BT>(J_BTAG, lead)));
+                    }
+                    if (sub >= 0) jet4(T, s, sub, r + R_J2);
+                    if (ta >= 0) {
+                        jet4(T, s, ta, r + R_T1);
+                        jet4(T, s, tb, r + R_T2);
+                        jet4(T, s, tc, r + R_T3);
+                    }
+                };
+                if (staged)
+                    write4(sc);
+                else
+                    write4(dc);
+                r[R_E] = static_cast<uint32_t>(e);
+                r[R_K] = static_cast<uint32_t>(k) | (pass ? 0x100u : 0u) | (static_cast<uint32_t>(min(nlep, 0xffff)) << 16);
+                r[R_NJ] = static_cast<uint32_t>(min(njet, 0xffff)) | (static_cast<uint32_t>(min(nbj, 0xffff)) << 16);
+                r[R_W] = __float_as_uint(w);
+                r[R_LPT] = __float_as_uint(lpt);
+                r[R_LETA] = __float_as_uint(leta);
+                r[R_LPHI] = __float_as_uint(lphi);
+                r[R_LISO] = __float_as_uint(liso);
+            }
+            __syncwarp();
+            qcount += m;
+        }
+        // this warp is done with the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty[b]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cs_[c] = ns_[c];
+            ct_[c] = nt_[c];
+        }
+        b ^= 1;
+    }
+    if (qcount > 0) flush(qcount);
+
+    if (SMEM_HIST) {
+        __syncthreads();
+        for (int i = tid; i < hist_n; i += E) {
+            const unsigned c = s_c[i];
+            if (c == 0u) continue;
+            atomicAdd(&out.counts[i], static_cast<unsigned long long>(c));
+            atomicAdd(&out.sumw[i], s_w[i]);
+            if (out.sumw2) atomicAdd(&out.sumw2[i], s_w2[i]);
+        }
+    }
+}
+
+// Launch parameters prepared by hepacc_run_chain for the typed launchers.
+struct LaunchArgs {
+    Layout layout;
+    const ChainParams* P;
+    ChainCols C;
+    const void *joff, *moff, *eoff;
+    hepacc_dtype offsets_type, btag_type;
+    int64_t n;
+    ChainOut out;
+    bool debug, smem_hist;
+    int block;
+    int grid;            // 0 = one block per SM
+    cudaStream_t stream;
+};
+
+template <typename T> struct Tag { using type = T; };
+
+struct Cache {
+    std::mutex mu;
+    std::unordered_map<const void*, int> smem_set;
+};
+inline Cache& cache() {
+    static Cache c;
+    return c;
+}
+
+template <typename K, typename... A>
+hepacc_status launch_chain(K kernel, int block, size_t smem, int64_t n, cudaStream_t stream, int grid_override,
+                           A... args) {
+    const DeviceInfo di = device_info();
+    if (smem > static_cast<size_t>(di.smem_optin)) return fail(HEPACC_ERR_INVALID_ARG, "chain shared memory too large");
+    {
+        std::lock_guard<std::mutex> g(cache().mu);
+        auto it = cache().smem_set.find(reinterpret_cast<const void*>(kernel));
+        if (it == cache().smem_set.end() || it->second < static_cast<int>(smem)) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            cache().smem_set[reinterpret_cast<const void*>(kernel)] = static_cast<int>(smem);
+        }
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return fail(HEPACC_ERR_INVALID_ARG, "chain kernel does not fit on an SM");
+    const int64_t ntiles = (n + block - 1) / block;
+    int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ntiles, static_cast<int64_t>(per_sm) * di.sms)));
+    if (grid_override > 0) grid = grid_override;
+    kernel<<<grid, block, smem, stream>>>(args...);
+    HEPACC_CHECK_LAUNCH("chain launch");
+    return HEPACC_OK;
+}
+
+template <typename KT>
+hepacc_status run_typed(const LaunchArgs& a) {
+    auto go = [&](auto bt, auto ot) -> hepacc_status {
+        using BT = typename decltype(bt)::type;
+        using O = typename decltype(ot)::type;
+        const O* jo = static_cast<const O*>(a.joff);
+        const O* mo = static_cast<const O*>(a.moff);
+        const O* eo = static_cast<const O*>(a.eoff);
+        const size_t smem = a.layout.total;
+        if (a.debug) {
+            if (a.smem_hist)
+                return launch_chain(k_chain<KT, BT, O, true, true>, a.block, smem, a.n, a.stream, a.grid, a.layout,
+                                    *a.P, a.C, jo, mo, eo, a.n, a.out);
+            return launch_chain(k_chain<KT, BT, O, true, false>, a.block, smem, a.n, a.stream, a.grid, a.layout, *a.P,
+                                a.C, jo, mo, eo, a.n, a.out);
+        }
+        if (a.smem_hist)
+            return launch_chain(k_chain<KT, BT, O, false, true>, a.block, smem, a.n, a.stream, a.grid, a.layout, *a.P,
+                                a.C, jo, mo, eo, a.n, a.out);
+        return launch_chain(k_chain<KT, BT, O, false, false>, a.block, smem, a.n, a.stream, a.grid, a.layout, *a.P, a.C,
+                            jo, mo, eo, a.n, a.out);
+    };
+    auto with_o = [&](auto bt) -> hepacc_status {
+        if (a.offsets_type == HEPACC_I32) return go(bt, Tag<int32_t>{});
+        return go(bt, Tag<int64_t>{});
+    };
+    if (a.btag_type == HEPACC_F32) return with_o(Tag<float>{});
+    return with_o(Tag<__half>{});
+}
+
+hepacc_status run_f32(const LaunchArgs& a);
+hepacc_status run_bf16(const LaunchArgs& a);
+hepacc_status run_f16(const LaunchArgs& a);
+unsigned int tu_error_f32(bool clear);
+unsigned int tu_error_bf16(bool clear);
+unsigned int tu_error_f16(bool clear);
+
+}  // namespace chain
+}  // namespace hepacc

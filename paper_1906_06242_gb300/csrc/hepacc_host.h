@@ -9,7 +9,7 @@
 #include <cstdio>
 #include <string>
 
-#include "../../include/hepacc.h"
+#include "hepacc.h"
 
 namespace hepacc {
 

@@ -8,6 +8,9 @@
 // Two stage buffers per warp: the copies of the next tile are in flight while
 // the lanes work on the current one. A tile whose span does not fit the
 // stage capacity is processed straight from global memory instead.
+//
+// Inside a tile every element index is 32-bit and relative to the tile's
+// first element of its collection.
 #pragma once
 
 #include "hepacc_device.cuh"
@@ -35,33 +38,51 @@ struct StageSpec {
 template <int NC>
 __host__ __device__ inline uint32_t stage_bytes_per_warp(const StageSpec<NC>& s) { return 2 * s.buf_bytes + 16; }
 
-template <int NCOLL, int kMaxCols>
-struct TileView {
-    int64_t e;                   // this lane's event
-    bool valid;                  // e < n
-    int64_t s[NCOLL], t[NCOLL];  // this lane's element range per collection
-    int64_t S[NCOLL];            // first element of the tile per collection
-    const unsigned char* colp[kMaxCols];   // element i of column c at colp[c] + (i - S[coll]) * es
-    bool staged;
+extern __shared__ __align__(128) unsigned char g_dyn_smem[];
 
+// This lane's event and element ranges inside the current tile.
+template <int NCOLL>
+struct TileRanges {
+    int64_t e;                   // event index
+    bool valid;                  // e < n
+    int rs[NCOLL], rt[NCOLL];    // [rs, rt): the event's elements, relative to S
+    int64_t S[NCOLL];            // absolute index of the tile's first element
+};
+
+// Column access for a staged tile: element r of column c is in shared memory.
+template <int NC>
+struct SmemCols {
+    uint32_t off[NC];            // byte offset of element 0 (relative to S) in dynamic shared memory
     template <typename T>
-    __device__ __forceinline__ T at(int c, int coll, int64_t i) const {
-        return reinterpret_cast<const T*>(colp[c])[i - S[coll]];
+    __device__ __forceinline__ T ld(int c, int r) const {
+        return *reinterpret_cast<const T*>(g_dyn_smem + off[c] + r * static_cast<int>(sizeof(T)));
     }
 };
 
-// Runs body(TileView&) for every tile this warp owns. Kernels that use it
-// need stage_bytes_per_warp(spec) * warps bytes of dynamic shared memory.
-template <typename OffT, int NCOLL, int kMaxCols, typename Body>
-__device__ __forceinline__ void tile_loop(const StageSpec<kMaxCols>& spec, const OffT* const (&offs)[NCOLL],
-                                          int64_t n, Body&& body) {
-    extern __shared__ __align__(128) unsigned char smem[];
+// Column access straight from global memory (tiles too large to stage).
+template <int NC>
+struct GlobCols {
+    const unsigned char* p[NC];  // address of element 0 (relative to S)
+    template <typename T>
+    __device__ __forceinline__ T ld(int c, int r) const {
+        return reinterpret_cast<const T*>(p[c])[r];
+    }
+};
+
+// Runs body(cols, ranges) for every tile this warp owns, with cols a
+// SmemCols (staged) or GlobCols. Kernels that use it need
+// stage_bytes_per_warp(spec) * warps bytes at the start of dynamic shared
+// memory.
+template <typename OffT, int NCOLL, int NC, typename Body>
+__device__ __forceinline__ void tile_loop(const StageSpec<NC>& spec, const OffT* const (&offs)[NCOLL], int64_t n,
+                                          Body&& body) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
-    unsigned char* wbuf = smem + static_cast<size_t>(warp) * 2 * spec.buf_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(nwarp) * 2 * spec.buf_bytes) + 2 * warp;
+    const uint32_t wbuf = static_cast<uint32_t>(warp) * 2u * spec.buf_bytes;     // offset in dynamic smem
+    uint64_t* bars = reinterpret_cast<uint64_t*>(g_dyn_smem + static_cast<size_t>(nwarp) * 2 * spec.buf_bytes) + 2 * warp;
     const uint32_t bar[2] = {smem_addr(bars), smem_addr(bars + 1)};
+    const uint32_t smem0 = smem_addr(g_dyn_smem);
     if (lane == 0) {
         mbar_init(bar[0], 1);
         mbar_init(bar[1], 1);
@@ -90,7 +111,7 @@ __device__ __forceinline__ void tile_loop(const StageSpec<kMaxCols>& spec, const
         bool fits = true;
         uint32_t total = 0;
 #pragma unroll
-        for (int c = 0; c < kMaxCols; ++c) {
+        for (int c = 0; c < NC; ++c) {
             if (c >= spec.ncol || spec.col[c].base == nullptr) continue;
             const ColSpec& cs = spec.col[c];
             const uintptr_t a = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
@@ -105,7 +126,7 @@ __device__ __forceinline__ void tile_loop(const StageSpec<kMaxCols>& spec, const
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(bar[b], total);
 #pragma unroll
-                for (int c = 0; c < kMaxCols; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     if (c >= spec.ncol || spec.col[c].base == nullptr) continue;
                     const ColSpec& cs = spec.col[c];
                     if (T[cs.coll] <= S[cs.coll]) continue;
@@ -113,8 +134,8 @@ __device__ __forceinline__ void tile_loop(const StageSpec<kMaxCols>& spec, const
                     const uintptr_t z = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
                     const uintptr_t a16 = a & ~uintptr_t(15);
                     const uint32_t bytes = static_cast<uint32_t>(((z + 15) & ~uintptr_t(15)) - a16);
-                    bulk_g2s(smem_addr(wbuf + b * spec.buf_bytes + cs.soff), reinterpret_cast<const void*>(a16),
-                             bytes, bar[b]);
+                    bulk_g2s(smem0 + wbuf + b * spec.buf_bytes + cs.soff, reinterpret_cast<const void*>(a16), bytes,
+                             bar[b]);
                 }
             } else {
                 mbar_arrive_expect_tx(bar[b], 0);
@@ -136,28 +157,37 @@ __device__ __forceinline__ void tile_loop(const StageSpec<kMaxCols>& spec, const
         }
         parity[b] ^= 1u;
 
-        TileView<NCOLL, kMaxCols> v;
-        v.e = tile * kTile + lane;
-        v.valid = v.e < n;
-        v.staged = cstaged;
+        TileRanges<NCOLL> r;
+        r.e = tile * kTile + lane;
+        r.valid = r.e < n;
 #pragma unroll
         for (int c = 0; c < NCOLL; ++c) {
-            v.s[c] = cs_[c];
-            v.t[c] = ct_[c];
-            v.S[c] = __shfl_sync(0xffffffffu, cs_[c], 0);
+            r.S[c] = __shfl_sync(0xffffffffu, cs_[c], 0);
+            r.rs[c] = static_cast<int>(cs_[c] - r.S[c]);
+            r.rt[c] = static_cast<int>(ct_[c] - r.S[c]);
         }
+        if (cstaged) {
+            SmemCols<NC> sc;
 #pragma unroll
-        for (int c = 0; c < kMaxCols; ++c) {
-            if (c >= spec.ncol || spec.col[c].base == nullptr) {
-                v.colp[c] = nullptr;
-                continue;
+            for (int c = 0; c < NC; ++c) {
+                sc.off[c] = 0;
+                if (c >= spec.ncol || spec.col[c].base == nullptr) continue;
+                const ColSpec& col = spec.col[c];
+                const uintptr_t a = reinterpret_cast<uintptr_t>(col.base) + static_cast<uintptr_t>(r.S[col.coll]) * col.es;
+                sc.off[c] = wbuf + b * spec.buf_bytes + col.soff + static_cast<uint32_t>(a & 15u);
             }
-            const ColSpec& cs = spec.col[c];
-            const uintptr_t a = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(v.S[cs.coll]) * cs.es;
-            v.colp[c] = cstaged ? wbuf + b * spec.buf_bytes + cs.soff + (a & 15u)
-                                : reinterpret_cast<const unsigned char*>(a);
+            body(sc, r);
+        } else {
+            GlobCols<NC> gc;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                gc.p[c] = nullptr;
+                if (c >= spec.ncol || spec.col[c].base == nullptr) continue;
+                const ColSpec& col = spec.col[c];
+                gc.p[c] = col.base + static_cast<uintptr_t>(r.S[col.coll]) * col.es;
+            }
+            body(gc, r);
         }
-        body(v);
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < NCOLL; ++c) {

@@ -55,16 +55,16 @@ template <typename T, typename OffT, typename OutT>
 __global__ void __launch_bounds__(kBlock) k_sum(Spec spec, const OffT* off, int64_t n,
                                                 const uint8_t* __restrict__ mask_rows, OutT* __restrict__ out) {
     const OffT* const offs[1] = {off};
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
-        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
+    const bool hm = spec.col[1].base != nullptr;
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+        if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
         using A = typename Acc<T>::type;
-        A acc = static_cast<A>(out[v.e]);
-        const bool hm = v.colp[1] != nullptr;
-        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
-            if (hm && !v.template at<uint8_t>(1, 0, i)) continue;
-            acc = acc_add<A, T>(acc, v.template at<T>(0, 0, i));
+        A acc = static_cast<A>(out[r.e]);
+        for (int i = r.rs[0]; i < r.rt[0]; ++i) {
+            if (hm && !C.template ld<uint8_t>(1, i)) continue;
+            acc = acc_add<A, T>(acc, C.template ld<T>(0, i));
         }
-        out[v.e] = static_cast<OutT>(acc);
+        out[r.e] = static_cast<OutT>(acc);
     });
 }
 
@@ -74,22 +74,22 @@ __global__ void __launch_bounds__(kBlock) k_minmax(Spec spec, const OffT* off, i
                                                    const uint8_t* __restrict__ mask_rows, float empty,
                                                    float* __restrict__ out, int32_t* __restrict__ arg) {
     const OffT* const offs[1] = {off};
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
-        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
-        const bool hm = v.colp[1] != nullptr;
-        int64_t bi = -1;
+    const bool hm = spec.col[1].base != nullptr;
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+        if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
+        int bi = -1;
         float best = empty;
-        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
-            if (hm && !v.template at<uint8_t>(1, 0, i)) continue;
-            const float x = Elem<T>::f(v.template at<T>(0, 0, i));
+        for (int i = r.rs[0]; i < r.rt[0]; ++i) {
+            if (hm && !C.template ld<uint8_t>(1, i)) continue;
+            const float x = Elem<T>::f(C.template ld<T>(0, i));
             if (x != x) continue;
             if (bi < 0 || (MAX ? x > best : x < best)) {
                 best = x;
                 bi = i;
             }
         }
-        if (out) out[v.e] = bi < 0 ? empty : best;
-        if (arg) arg[v.e] = bi < 0 ? -1 : static_cast<int32_t>(bi - v.s[0]);
+        if (out) out[r.e] = bi < 0 ? empty : best;
+        if (arg) arg[r.e] = bi < 0 ? -1 : bi - r.rs[0];
     });
 }
 
@@ -100,14 +100,15 @@ __global__ void __launch_bounds__(kBlock) k_get(Spec spec, const OffT* off, int6
                                                 const uint8_t* __restrict__ mask_rows, float dflt,
                                                 float* __restrict__ out, int32_t* __restrict__ oidx) {
     const OffT* const offs[1] = {off};
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
-        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
-        const bool hm = v.colp[1] != nullptr;
-        const int64_t want = nth ? nth[v.e] : nth_scalar;
-        int64_t seen = 0, found = -1;
+    const bool hm = spec.col[1].base != nullptr;
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+        if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
+        const int64_t want = nth ? nth[r.e] : nth_scalar;
+        int64_t seen = 0;
+        int found = -1;
         if (want >= 0) {
-            for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
-                if (hm && !v.template at<uint8_t>(1, 0, i)) continue;
+            for (int i = r.rs[0]; i < r.rt[0]; ++i) {
+                if (hm && !C.template ld<uint8_t>(1, i)) continue;
                 if (seen == want) {
                     found = i;
                     break;
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(kBlock) k_get(Spec spec, const OffT* off, int6
                 ++seen;
             }
         }
-        if (out) out[v.e] = found < 0 ? dflt : Elem<T>::f(v.template at<T>(0, 0, found));
-        if (oidx) oidx[v.e] = found < 0 ? -1 : static_cast<int32_t>(found - v.s[0]);
+        if (out) out[r.e] = found < 0 ? dflt : Elem<T>::f(C.template ld<T>(0, found));
+        if (oidx) oidx[r.e] = found < 0 ? -1 : found - r.rs[0];
     });
 }
 
@@ -127,25 +128,25 @@ __global__ void __launch_bounds__(kBlock) k_deltar(Spec spec, const OffT* off1, 
                                                    const uint8_t* __restrict__ mask_rows, float cut,
                                                    uint8_t* __restrict__ mask_out) {
     const OffT* const offs[2] = {off1, off2};
-    tile_loop<OffT, 2, NC>(spec, offs, n, [&](const TileView<2, NC>& v) {
-        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
-        const bool h1 = v.colp[2] != nullptr, h2 = v.colp[5] != nullptr;
-        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
-            bool keep = h1 ? v.template at<uint8_t>(2, 0, i) != 0 : true;
+    const bool h1 = spec.col[2].base != nullptr, h2 = spec.col[5].base != nullptr;
+    tile_loop<OffT, 2, NC>(spec, offs, n, [&](const auto& C, const TileRanges<2>& r) {
+        if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
+        for (int i = r.rs[0]; i < r.rt[0]; ++i) {
+            bool keep = h1 ? C.template ld<uint8_t>(2, i) != 0 : true;
             if (keep) {
-                const float e1 = Elem<T1>::f(v.template at<T1>(0, 0, i));
-                const float p1 = Elem<T1>::f(v.template at<T1>(1, 0, i));
-                for (int64_t j = v.s[1]; j < v.t[1]; ++j) {
-                    if (h2 && !v.template at<uint8_t>(5, 1, j)) continue;
-                    const float d = dr2_f32(e1, p1, Elem<T2>::f(v.template at<T2>(3, 1, j)),
-                                            Elem<T2>::f(v.template at<T2>(4, 1, j)));
+                const float e1 = Elem<T1>::f(C.template ld<T1>(0, i));
+                const float p1 = Elem<T1>::f(C.template ld<T1>(1, i));
+                for (int j = r.rs[1]; j < r.rt[1]; ++j) {
+                    if (h2 && !C.template ld<uint8_t>(5, j)) continue;
+                    const float d = dr2_f32(e1, p1, Elem<T2>::f(C.template ld<T2>(3, j)),
+                                            Elem<T2>::f(C.template ld<T2>(4, j)));
                     if (d < cut) {
                         keep = false;
                         break;
                     }
                 }
             }
-            mask_out[i] = keep ? 1 : 0;
+            mask_out[r.S[0] + i] = keep ? 1 : 0;
         }
     });
 }
@@ -159,21 +160,24 @@ __global__ void __launch_bounds__(kBlock) k_trijet(Spec spec, const OffT* off, i
                                                    const uint8_t* __restrict__ mask_rows, float* __restrict__ om,
                                                    float* __restrict__ opt, int32_t* __restrict__ oidx) {
     const OffT* const offs[1] = {off};
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const TileView<1, NC>& v) {
-        if (!v.valid || (mask_rows && !mask_rows[v.e])) return;
-        const bool hm = v.colp[4] != nullptr;
+    const bool hm = spec.col[4].base != nullptr;
+    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+        if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
+        auto pt_of = [&](int i) { return Elem<T>::f(C.template ld<T>(0, i)); };
+        auto phi_of = [&](int i) { return Elem<T>::f(C.template ld<T>(2, i)); };
+        auto on = [&](int i) { return !hm || C.template ld<uint8_t>(4, i) != 0; };
         float px[kTriLocal], py[kTriLocal];
         int32_t li[kTriLocal];
         int cnt = 0;
-        for (int64_t i = v.s[0]; i < v.t[0]; ++i) {
-            if (hm && !v.template at<uint8_t>(4, 0, i)) continue;
+        for (int i = r.rs[0]; i < r.rt[0]; ++i) {
+            if (!on(i)) continue;
             if (cnt < kTriLocal) {
                 float sn, cs;
-                const float pt = Elem<T>::f(v.template at<T>(0, 0, i));
-                sincosf(Elem<T>::f(v.template at<T>(2, 0, i)), &sn, &cs);
+                const float pt = pt_of(i);
+                sincosf(phi_of(i), &sn, &cs);
                 px[cnt] = pt * cs;
                 py[cnt] = pt * sn;
-                li[cnt] = static_cast<int32_t>(i - v.s[0]);
+                li[cnt] = i - r.rs[0];
             }
             ++cnt;
         }
@@ -196,29 +200,29 @@ __global__ void __launch_bounds__(kBlock) k_trijet(Spec spec, const OffT* off, i
                 }
         } else if (cnt > kTriLocal) {
             // many objects: enumerate the masked-in elements directly
-            for (int64_t a = v.s[0]; a < v.t[0]; ++a) {
-                if (hm && !v.template at<uint8_t>(4, 0, a)) continue;
+            for (int a = r.rs[0]; a < r.rt[0]; ++a) {
+                if (!on(a)) continue;
                 float sa, ca;
-                sincosf(Elem<T>::f(v.template at<T>(2, 0, a)), &sa, &ca);
-                const float pa = Elem<T>::f(v.template at<T>(0, 0, a));
-                for (int64_t b = a + 1; b < v.t[0]; ++b) {
-                    if (hm && !v.template at<uint8_t>(4, 0, b)) continue;
+                sincosf(phi_of(a), &sa, &ca);
+                const float pa = pt_of(a);
+                for (int b = a + 1; b < r.rt[0]; ++b) {
+                    if (!on(b)) continue;
                     float sb, cb;
-                    sincosf(Elem<T>::f(v.template at<T>(2, 0, b)), &sb, &cb);
-                    const float pb = Elem<T>::f(v.template at<T>(0, 0, b));
+                    sincosf(phi_of(b), &sb, &cb);
+                    const float pb = pt_of(b);
                     const float sx = pa * ca + pb * cb, sy = pa * sa + pb * sb;
-                    for (int64_t c = b + 1; c < v.t[0]; ++c) {
-                        if (hm && !v.template at<uint8_t>(4, 0, c)) continue;
+                    for (int c = b + 1; c < r.rt[0]; ++c) {
+                        if (!on(c)) continue;
                         float sc, cc;
-                        sincosf(Elem<T>::f(v.template at<T>(2, 0, c)), &sc, &cc);
-                        const float pc = Elem<T>::f(v.template at<T>(0, 0, c));
+                        sincosf(phi_of(c), &sc, &cc);
+                        const float pc = pt_of(c);
                         const float tx = sx + pc * cc, ty = sy + pc * sc;
                         const float val = tx * tx + ty * ty;
                         if (val > best) {
                             best = val;
-                            ba = static_cast<int32_t>(a - v.s[0]);
-                            bb = static_cast<int32_t>(b - v.s[0]);
-                            bc = static_cast<int32_t>(c - v.s[0]);
+                            ba = a - r.rs[0];
+                            bb = b - r.rs[0];
+                            bc = c - r.rs[0];
                         }
                     }
                 }
@@ -230,19 +234,19 @@ __global__ void __launch_bounds__(kBlock) k_trijet(Spec spec, const OffT* off, i
             const int32_t ix[3] = {ba, bb, bc};
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const int64_t i = v.s[0] + ix[q];
-                o[q] = mass_obj(Elem<T>::f(v.template at<T>(0, 0, i)), Elem<T>::f(v.template at<T>(1, 0, i)),
-                                Elem<T>::f(v.template at<T>(2, 0, i)), Elem<T>::f(v.template at<T>(3, 0, i)));
+                const int i = r.rs[0] + ix[q];
+                o[q] = mass_obj(pt_of(i), Elem<T>::f(C.template ld<T>(1, i)), phi_of(i),
+                                Elem<T>::f(C.template ld<T>(3, i)));
             }
             m = mass3obj(o[0], o[1], o[2]);
             ptj = sqrtf(best);
         }
-        if (om) om[v.e] = m;
-        if (opt) opt[v.e] = ptj;
+        if (om) om[r.e] = m;
+        if (opt) opt[r.e] = ptj;
         if (oidx) {
-            oidx[3 * v.e] = ba;
-            oidx[3 * v.e + 1] = bb;
-            oidx[3 * v.e + 2] = bc;
+            oidx[3 * r.e] = ba;
+            oidx[3 * r.e + 1] = bb;
+            oidx[3 * r.e + 2] = bc;
         }
     });
 }

@@ -276,7 +276,8 @@ class EventBatchC(ctypes.Structure):
                 ("mu_tight", _c_void_p),
                 ("el_pt", _c_void_p), ("el_eta", _c_void_p), ("el_phi", _c_void_p), ("el_iso", _c_void_p),
                 ("el_tight", _c_void_p),
-                ("weight", _c_void_p)]
+                ("weight", _c_void_p), ("jets_per_event", ctypes.c_float),
+                ("leptons_per_event", ctypes.c_float)]
 
 
 class ChainConfigC(ctypes.Structure):
@@ -348,6 +349,9 @@ class DeviceBatch:
         for name in COLUMNS:
             setattr(c, name, _addr(self.cols[name]))
         c.weight = _addr(self.weight)
+        n = max(1, self.n_events)
+        c.jets_per_event = self.cols["jet_pt"].numel() / n
+        c.leptons_per_event = (self.cols["mu_pt"].numel() + self.cols["el_pt"].numel()) / n
         self._c = c
         return c
 
