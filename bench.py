@@ -89,7 +89,7 @@ def chain_traffic(kernel_src_sha):
 def kernel_source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1906_06242_gb300", "csrc")
-    for fn in ("chain.cu", "hepacc_tiles.cuh", "hepacc_device.cuh"):
+    for fn in ("chain.cu", "chain_kernel.cuh", "hepacc_tiles.cuh", "hepacc_device.cuh"):
         h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
