@@ -249,8 +249,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         # the one exchange of the sharded chain: sum of the histograms
-        dist.all_reduce(out.counts)
-        dist.all_reduce(out.sumw)
+        from paper_1906_06242_gb300 import shard
+        shard.allreduce_histograms([out.counts, out.sumw, out.sumw2])
     ms_per_step = total_ms / args.steps
     value = world * batch.n_events / (ms_per_step * 1e-3)
     avg_kernel_ms = sum(kern_ms) / len(kern_ms)
@@ -360,6 +360,13 @@ def secondary_forms(H, synth, batch, torch, stream):
     ms = timeit(lambda: perop.run_chain_per_op(db, cfg, out, ws, stream=stream), k=5, w=1)
     res["per_op_fp32"] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms}
     del ws, db
+    # reference decisions and histograms of the FP32 columns (per-event outputs)
+    db = H.DeviceBatch.from_host(batch)
+    ref = H.ChainOutputs(cfg, batch.n_events, per_event=True)
+    H.hepacc_run_chain(db, cfg, ref, stream=stream)
+    ref_pass = ref.ev_pass.clone()
+    ref_counts = ref.counts.clone()
+    del ref, db
     for fmt in ("bf16", "f16"):
         hb = synth.reduced_precision(batch, fmt)
         dh = H.DeviceBatch.from_host(hb)
@@ -367,9 +374,18 @@ def secondary_forms(H, synth, batch, torch, stream):
         s = (dh.c_struct(), cfg.c_struct(), oh.c_struct())
         ms = timeit(lambda: H.hepacc_run_chain(dh, cfg, oh, stream=stream, _structs=s), k=20, w=3)
         nbytes = algorithmic_bytes(hb)
+        # changed event decisions and histogram deltas against the FP32 columns
+        pe = H.ChainOutputs(cfg, batch.n_events, per_event=True)
+        H.hepacc_run_chain(dh, cfg, pe, stream=stream)
+        changed = int((pe.ev_pass != ref_pass).sum().item())
+        l1 = int((pe.counts - ref_counts).abs().sum().item())
         res[f"fused_{fmt}"] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms,
-                               "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}
-        del dh
+                               "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9,
+                               "algorithmic_bytes": int(nbytes),
+                               "changed_decisions_vs_f32": changed,
+                               "passing_f32": int(ref_pass.sum().item()),
+                               "hist_count_l1_vs_f32": l1}
+        del dh, pe
     return res
 
 

@@ -82,6 +82,13 @@ const char *hepacc_status_string(hepacc_status s);
  * fails (bit 1). Synchronises the device. *flags receives the word. */
 hepacc_status hepacc_device_error(uint32_t *flags);
 
+/* Self-test of the bounded-wait path: launches one thread that waits on an
+ * mbarrier nothing ever completes, giving up after about limit_cycles SM
+ * clocks (1 <= limit_cycles <= 2^31). The kernel then sets bit 0 of the
+ * device error word and returns, leaving the context usable; read it with
+ * hepacc_device_error(). Asynchronous. */
+hepacc_status hepacc_selftest_wait_timeout(int64_t limit_cycles, hepacc_stream stream);
+
 /* Offsets check (Section II layout): offsets[0] >= 0, non-decreasing, and
  * offsets[n_rows] <= content_len. *first_bad (a DEVICE int64) receives the
  * smallest event index i whose offsets[i+1] breaks a rule (-1 if none; -2 if

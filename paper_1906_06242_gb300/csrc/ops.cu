@@ -398,6 +398,15 @@ __global__ void k_validate(const OffT* off, int64_t n, int64_t m, unsigned long 
     }
 }
 
+// One thread waits on an mbarrier that is never completed (bounded wait).
+__global__ void k_wait_timeout(long long limit_cycles) {
+    __shared__ uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    mbar_init(b, 1);
+    fence_mbar_init();
+    mbar_wait_bounded(b, 0, limit_cycles);
+}
+
 __global__ void k_validate_init(const void* off, int ot64, unsigned long long* first_bad) {
     *first_bad = ~0ull;
     const int64_t o0 = ot64 ? *static_cast<const int64_t*>(off) : *static_cast<const int32_t*>(off);
@@ -781,6 +790,13 @@ hepacc_status hepacc_fill_histogram(const void* data, hepacc_dtype dt, const flo
         HEPACC_CHECK_LAUNCH("fill_histogram launch");
         return HEPACC_OK;
     });
+}
+
+hepacc_status hepacc_selftest_wait_timeout(int64_t limit_cycles, hepacc_stream stream) {
+    HEPACC_CHECK(limit_cycles >= 1 && limit_cycles <= (int64_t(1) << 31), "limit_cycles must be in [1, 2^31]");
+    k_wait_timeout<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(static_cast<long long>(limit_cycles));
+    HEPACC_CHECK_LAUNCH("selftest launch");
+    return HEPACC_OK;
 }
 
 hepacc_status hepacc_validate_offsets(const void* offsets, hepacc_dtype ot, int64_t n, int64_t content_len,

@@ -62,7 +62,8 @@ def load(build_if_missing: bool = True):
     for name in ("hepacc_sum_in_offsets", "hepacc_max_in_offsets", "hepacc_min_in_offsets",
                  "hepacc_get_in_offsets", "hepacc_set_in_offsets", "hepacc_select_range", "hepacc_scale",
                  "hepacc_mask_deltar", "hepacc_fill_histogram", "hepacc_pair_mass", "hepacc_max_pt_trijet",
-                 "hepacc_run_chain", "hepacc_validate_offsets", "hepacc_device_error"):
+                 "hepacc_run_chain", "hepacc_validate_offsets", "hepacc_device_error",
+                 "hepacc_selftest_wait_timeout"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -117,6 +118,11 @@ def device_error() -> int:
     v = ctypes.c_uint32(0)
     _check(load().hepacc_device_error(ctypes.byref(v)))
     return v.value
+
+
+def hepacc_selftest_wait_timeout(limit_cycles=1_000_000, stream=None):
+    """Run the bounded-wait self-test kernel (sets the device error word)."""
+    _check(load().hepacc_selftest_wait_timeout(_i64(limit_cycles), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -287,3 +287,27 @@ def test_validate_offsets(H):
     neg = off.astype(np.int32).copy()
     neg[0] = -1
     assert int(host(H.hepacc_validate_offsets(dev(neg), 12))[0]) == -2
+
+
+def test_bounded_wait_reports_timeout(H):
+    # a wait that nothing completes gives up, sets the error word, and the
+    # context stays usable
+    assert H.device_error() == 0
+    H.hepacc_selftest_wait_timeout(200_000)
+    assert H.device_error() & 1
+    assert H.device_error() == 0
+    off = torch.tensor([0, 2, 5], dtype=torch.int64, device="cuda")
+    x = torch.arange(5, dtype=torch.float32, device="cuda")
+    np.testing.assert_array_equal(host(H.hepacc_sum_in_offsets(x, off)), [1.0, 9.0])
+
+
+def test_invalid_arguments_rejected(H):
+    off = torch.tensor([0, 2, 5], dtype=torch.int64, device="cuda")
+    x = torch.arange(5, dtype=torch.float32, device="cuda")
+    with pytest.raises(H.HepaccError) as ei:
+        H.hepacc_sum_in_offsets(x, off, out=torch.zeros(2, dtype=torch.int32, device="cuda"))
+    assert ei.value.status == 2
+    with pytest.raises(H.HepaccError):
+        H.hepacc_fill_histogram(x, torch.zeros(1, dtype=torch.float32, device="cuda"))
+    with pytest.raises(H.HepaccError):
+        H.hepacc_selftest_wait_timeout(0)
