@@ -304,6 +304,55 @@ typedef struct {
 hepacc_status hepacc_run_chain(const hepacc_event_batch *batch, const hepacc_chain_config *config,
                                const hepacc_chain_outputs *out, hepacc_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched chain plans (Section IV: the benchmark runs the chain over many
+ * samples of uneven size, each with its jet-pt variations)
+ * ------------------------------------------------------------------------- */
+
+/* Opaque plan: samples, their outputs, the kernel configuration chosen for
+ * them and (optionally) a CUDA graph of the launches. */
+typedef struct hepacc_plan hepacc_plan;
+
+#define HEPACC_PLAN_AUTOTUNE 1          /* time the candidate configurations on the samples, keep the fastest */
+#define HEPACC_PLAN_GRAPH 2             /* capture the launches once; runs replay the graph */
+/* Candidate histogram placements (none of these flags = all of them). */
+#define HEPACC_PLAN_HIST_BLOCK 4        /* block-private shared memory */
+#define HEPACC_PLAN_HIST_CLUSTER8 8     /* shared memory of a cluster of 8 blocks */
+#define HEPACC_PLAN_HIST_CLUSTER16 16   /* shared memory of a cluster of 16 blocks */
+#define HEPACC_PLAN_HIST_GLOBAL 32      /* global memory */
+
+/* Builds a plan that runs the chain of hepacc_run_chain over samples[0..n)
+ * with one configuration, sixteen samples per persistent launch: every block
+ * walks through the samples in turn, so blocks idle on a small sample move
+ * to the next. Sample i adds to outputs[i] (counts, sumw, sumw2 as in
+ * hepacc_run_chain; per-event arrays must be NULL). All samples use I64
+ * offsets and the same kin_type and btag_type (F32 with F32, F16 with F16
+ * or BF16). Histogram placement is a kernel configuration: block-private
+ * shared memory, shared memory spread over a cluster of 8 or 16 blocks
+ * (updated through distributed shared memory), or global memory. Without
+ * HEPACC_PLAN_AUTOTUNE the first candidate placement (HEPACC_PLAN_HIST_*)
+ * that fits, in that order, is taken; with it,
+ * every candidate is run three times on the samples (DEVICE pointers given
+ * here must be valid), the fastest kept, and the outputs cleared to zero
+ * afterwards, on `stream`, which the call synchronises. config is HOST
+ * memory and copied; the sample and output structs are copied; the device
+ * buffers they point to must stay valid for the plan's life. *plan is NULL
+ * on error. */
+hepacc_status hepacc_plan_create(const hepacc_chain_config *config, int32_t n_samples,
+                                 const hepacc_event_batch *samples, const hepacc_chain_outputs *outputs,
+                                 int32_t flags, hepacc_stream stream, hepacc_plan **plan);
+
+/* Runs the plan once on `stream` (outputs accumulate). Not thread-safe on
+ * one plan; two runs of one plan on different streams race on its outputs. */
+hepacc_status hepacc_plan_run(hepacc_plan *plan, hepacc_stream stream);
+
+/* Writes a one-line JSON description of the chosen configuration into
+ * buf[0..len) (NUL-terminated, truncated to fit). */
+hepacc_status hepacc_plan_describe(const hepacc_plan *plan, char *buf, int32_t len);
+
+/* Frees the plan (NULL is allowed); outputs and inputs are not touched. */
+void hepacc_plan_destroy(hepacc_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,45 +1,28 @@
-// Host entry point of the fused chain: validates the call, prepares the
-// kernel parameters (cuts, scales, histogram edges, stage layout) and picks
-// the shared-memory layout, then launches the kernel for the column types.
+// Host side of the fused chain: validates calls, prepares the kernel
+// parameters (cuts, scales, histogram edges), chooses the shared-memory
+// layout and the histogram placement and launches the kernel for the column
+// types; batched plans (many samples per launch, autotuned, replayed as a
+// CUDA graph).
 #include <cmath>
+#include <new>
+#include <vector>
 
 #include "chain_kernel.cuh"
 
 namespace hepacc {
 
 unsigned int tu_error_chain(bool clear) {
-    return chain::tu_error_f32(clear) | chain::tu_error_bf16(clear) | chain::tu_error_f16(clear);
+    return chain::tu_error_f32(clear) | chain::tu_error_bf16(clear) | chain::tu_error_f16(clear) |
+           chain::tu_error_batched_f32(clear) | chain::tu_error_batched_bf16(clear) |
+           chain::tu_error_batched_f16(clear);
 }
 
 namespace chain {
+namespace {
 
-// Tunables of the chain launch (set by the autotuner; 0 = default).
-struct ChainTuning {
-    int jet_cap;     // stage capacity for jets, elements per warp tile
-    int lep_cap;     // stage capacity per lepton collection
-    int grid;        // blocks (0 = resident blocks x SMs)
-    int warps;       // upper bound of warps per block (0 = 16)
-};
-ChainTuning g_tuning = {0, 0, 0, 0};
-
-
-}  // namespace chain
-}  // namespace hepacc
-
-using namespace hepacc;
-using namespace hepacc::chain;
-
-extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hepacc_chain_config* cfg,
-                                          const hepacc_chain_outputs* out, hepacc_stream stream) {
-    if (!b || !cfg || !out) return fail(HEPACC_ERR_INVALID_ARG, "batch, config and outputs are required");
-    if (b->n_events < 0) return fail(HEPACC_ERR_INVALID_ARG, "n_events < 0");
+hepacc_status make_params(const hepacc_chain_config* cfg, ChainParams& P) {
     if (cfg->n_var < 1 || cfg->n_var > HEPACC_MAX_VARIATIONS) return fail(HEPACC_ERR_INVALID_ARG, "n_var out of range");
     if (!cfg->scales || !cfg->edges) return fail(HEPACC_ERR_INVALID_ARG, "config scales and edges are required");
-    if (!out->counts || !out->sumw) return fail(HEPACC_ERR_INVALID_ARG, "counts and sumw are required");
-    if (!is_offsets_type(b->offsets_type)) return fail(HEPACC_ERR_DTYPE, "offsets must be I32 or I64");
-    if (!is_float_type(b->kin_type)) return fail(HEPACC_ERR_DTYPE, "kin_type must be F32, F16 or BF16");
-    if (b->btag_type != HEPACC_F32 && b->btag_type != HEPACC_F16) return fail(HEPACC_ERR_DTYPE, "btag_type must be F32 or F16");
-    ChainParams P;
     std::memset(&P, 0, sizeof P);
     P.lep_pt_min = cfg->lep_pt_min;
     P.lep_abseta_max = cfg->lep_abseta_max;
@@ -68,129 +51,437 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     }
     P.n_edges = ne;
     P.total_bins = nbt;
-    const int64_t n = b->n_events;
-    if (n == 0) return HEPACC_OK;
-    const bool debug = out->ev_pass || out->ev_nlep || out->ev_njet || out->ev_nb || out->ev_idx || out->ev_vars;
-    if (!b->jet_offsets || !b->mu_offsets || !b->el_offsets || !b->weight || !b->jet_pt || !b->jet_eta ||
-        !b->jet_phi || !b->jet_mass || !b->jet_btag || !b->mu_pt || !b->mu_eta || !b->mu_phi || !b->mu_iso ||
-        !b->mu_tight || !b->el_pt || !b->el_eta || !b->el_phi || !b->el_iso || !b->el_tight)
+    return HEPACC_OK;
+}
+
+hepacc_status check_batch(const hepacc_event_batch* b) {
+    if (b->n_events < 0) return fail(HEPACC_ERR_INVALID_ARG, "n_events < 0");
+    if (b->n_events >= (int64_t(1) << 31)) return fail(HEPACC_ERR_INVALID_ARG, "at most 2^31 - 1 events per sample");
+    if (!is_offsets_type(b->offsets_type)) return fail(HEPACC_ERR_DTYPE, "offsets must be I32 or I64");
+    if (!is_float_type(b->kin_type)) return fail(HEPACC_ERR_DTYPE, "kin_type must be F32, F16 or BF16");
+    if (b->btag_type != HEPACC_F32 && b->btag_type != HEPACC_F16) return fail(HEPACC_ERR_DTYPE, "btag_type must be F32 or F16");
+    if (b->n_events > 0 &&
+        (!b->jet_offsets || !b->mu_offsets || !b->el_offsets || !b->weight || !b->jet_pt || !b->jet_eta ||
+         !b->jet_phi || !b->jet_mass || !b->jet_btag || !b->mu_pt || !b->mu_eta || !b->mu_phi || !b->mu_iso ||
+         !b->mu_tight || !b->el_pt || !b->el_eta || !b->el_phi || !b->el_iso || !b->el_tight))
         return fail(HEPACC_ERR_INVALID_ARG, "a batch column is NULL");
+    return HEPACC_OK;
+}
 
-    ChainOut o;
-    o.counts = reinterpret_cast<unsigned long long*>(out->counts);
-    o.sumw = out->sumw;
-    o.sumw2 = out->sumw2;
-    o.ev_pass = out->ev_pass;
-    o.ev_nlep = out->ev_nlep;
-    o.ev_njet = out->ev_njet;
-    o.ev_nb = out->ev_nb;
-    o.ev_idx = out->ev_idx;
-    o.ev_vars = out->ev_vars;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+bool has_per_event(const hepacc_chain_outputs* o) {
+    return o->ev_pass || o->ev_nlep || o->ev_njet || o->ev_nb || o->ev_idx || o->ev_vars;
+}
 
-    if (n >= (int64_t(1) << 31)) return fail(HEPACC_ERR_INVALID_ARG, "at most 2^31 - 1 events per call");
-    ChainCols C;
-    C.jet_pt = b->jet_pt; C.jet_eta = b->jet_eta; C.jet_phi = b->jet_phi; C.jet_mass = b->jet_mass;
-    C.jet_btag = b->jet_btag;
-    C.mu_pt = b->mu_pt; C.mu_eta = b->mu_eta; C.mu_phi = b->mu_phi; C.mu_iso = b->mu_iso; C.mu_tight = b->mu_tight;
-    C.el_pt = b->el_pt; C.el_eta = b->el_eta; C.el_phi = b->el_phi; C.el_iso = b->el_iso; C.el_tight = b->el_tight;
-    C.weight = b->weight;
+void make_sample(const hepacc_event_batch* b, const hepacc_chain_outputs* out, SampleDesc& d) {
+    std::memset(&d, 0, sizeof d);
+    d.col[J_PT] = b->jet_pt;
+    d.col[J_ETA] = b->jet_eta;
+    d.col[J_PHI] = b->jet_phi;
+    d.col[J_MASS] = b->jet_mass;
+    d.col[J_BTAG] = b->jet_btag;
+    d.col[M_PT] = b->mu_pt;
+    d.col[M_ETA] = b->mu_eta;
+    d.col[M_PHI] = b->mu_phi;
+    d.col[M_ISO] = b->mu_iso;
+    d.col[M_TIGHT] = b->mu_tight;
+    d.col[E_PT] = b->el_pt;
+    d.col[E_ETA] = b->el_eta;
+    d.col[E_PHI] = b->el_phi;
+    d.col[E_ISO] = b->el_iso;
+    d.col[E_TIGHT] = b->el_tight;
+    d.weight = b->weight;
+    d.off[0] = b->jet_offsets;
+    d.off[1] = b->mu_offsets;
+    d.off[2] = b->el_offsets;
+    d.n = b->n_events;
+    d.out.counts = reinterpret_cast<unsigned long long*>(out->counts);
+    d.out.sumw = out->sumw;
+    d.out.sumw2 = out->sumw2;
+    d.out.ev_pass = out->ev_pass;
+    d.out.ev_nlep = out->ev_nlep;
+    d.out.ev_njet = out->ev_njet;
+    d.out.ev_nb = out->ev_nb;
+    d.out.ev_idx = out->ev_idx;
+    d.out.ev_vars = out->ev_vars;
+}
 
-    // Shared-memory layout for tiles of E events: stage capacities from the
-    // mean objects per event (tiles that do not fit are read from global
-    // memory), two stages, a 32-slot queue per warp and, when they fit, the
-    // block-private histograms; the largest E (multiple of 32, <= 384) that
-    // fits wins, preferring shared-memory histograms.
-    const double lam_j = b->jets_per_event > 0 ? b->jets_per_event : 6.0;
-    const double lam_l = b->leptons_per_event > 0 ? b->leptons_per_event : 1.5;
-    const size_t kes = dtype_size(b->kin_type), bes = dtype_size(b->btag_type);
-    const DeviceInfo di = device_info();
-    auto layout_for = [&](int E, bool with_hist, Layout& L) -> bool {
-        std::memset(&L, 0, sizeof L);
-        auto cap_of = [&](double lam) {
-            const double m = E * lam;
-            return static_cast<uint32_t>(((static_cast<size_t>(m + 4.0 * std::sqrt(m) + 64.0)) + 31) & ~size_t(31));
-        };
-        const uint32_t cj = cap_of(lam_j), cl = cap_of(lam_l);
-        uint32_t off = 0;
-        auto add = [&](int c, const void* base, size_t es, int coll, uint32_t cap) {
-            ColSpec& cs = L.col[c];
-            cs.base = static_cast<const unsigned char*>(base);
-            cs.es = static_cast<uint32_t>(es);
-            cs.coll = static_cast<uint32_t>(coll);
-            cs.cap = static_cast<uint32_t>((cap * es + 32 + 15) & ~size_t(15));
-            cs.soff = off;
-            off += cs.cap;
-        };
-        add(J_PT, b->jet_pt, kes, 0, cj);
-        add(J_ETA, b->jet_eta, kes, 0, cj);
-        add(J_PHI, b->jet_phi, kes, 0, cj);
-        add(J_MASS, b->jet_mass, kes, 0, cj);
-        add(J_BTAG, b->jet_btag, bes, 0, cj);
-        add(M_PT, b->mu_pt, kes, 1, cl);
-        add(M_ETA, b->mu_eta, kes, 1, cl);
-        add(M_PHI, b->mu_phi, kes, 1, cl);
-        add(M_ISO, b->mu_iso, 4, 1, cl);
-        add(M_TIGHT, b->mu_tight, 1, 1, cl);
-        add(E_PT, b->el_pt, kes, 2, cl);
-        add(E_ETA, b->el_eta, kes, 2, cl);
-        add(E_PHI, b->el_phi, kes, 2, cl);
-        add(E_ISO, b->el_iso, 4, 2, cl);
-        add(E_TIGHT, b->el_tight, 1, 2, cl);
-        auto up = [](size_t x) { return static_cast<uint32_t>((x + 127) & ~size_t(127)); };
-        L.stage_bytes = up(kHdr + off);
-        size_t at = 2 * static_cast<size_t>(L.stage_bytes);
-        L.bars = static_cast<uint32_t>(at);
-        at += 32 + 48 + 16;   // four mbarriers, spans of the next tile
-        L.edges = static_cast<uint32_t>(at);
-        at += static_cast<size_t>((P.n_edges + 3) & ~3) * 4;
-        L.queue = static_cast<uint32_t>(at);
-        at += static_cast<size_t>(E) * R_WORDS * 4;
-        L.acc_words = static_cast<int>(cj / 32 + 2);
-        L.acc = static_cast<uint32_t>(at);
-        at += static_cast<size_t>(E / 32) * L.acc_words * 4;
-        L.tri = static_cast<uint32_t>(at);
-        at += 256;
-        at = (at + 15) & ~size_t(15);
-        L.hist = static_cast<uint32_t>(at);
-        if (with_hist) at += static_cast<size_t>(P.n_var) * P.total_bins * (8 + 8 + 4);
-        L.total = static_cast<uint32_t>((at + 15) & ~size_t(15));
-        return L.total <= static_cast<size_t>(di.smem_optin);
+// Shared-memory layout for blocks of E threads (tiles of E events): stage
+// capacities from the mean objects per event (tiles that do not fit are read
+// from global memory), two stages, a 32-slot queue and jet acceptance flags
+// per warp, and the histograms of the placement (all of them in H_SMEM, a
+// 1/cluster slice in H_CLUSTER, none in H_GLOBAL). Returns whether it fits.
+bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_t kes, size_t bes,
+                const ChainParams& P, Layout& L) {
+    std::memset(&L, 0, sizeof L);
+    auto cap_of = [&](double lam) {
+        const double m = E * lam;
+        return static_cast<uint32_t>(((static_cast<size_t>(m + 4.0 * std::sqrt(m) + 64.0)) + 31) & ~size_t(31));
     };
-    const int max_e = std::min(kMaxThreads, g_tuning.warps > 0 ? 32 * g_tuning.warps : kMaxThreads);
-    Layout L;
-    int E = 0;
-    bool smem_hist = false;
-    for (int e = max_e; e >= 128 && E == 0; e -= 32)
-        if (layout_for(e, true, L)) {
-            E = e;
-            smem_hist = true;
-        }
-    for (int e = max_e; e >= 32 && E == 0; e -= 32)
-        if (layout_for(e, false, L)) E = e;
-    if (E == 0) return fail(HEPACC_ERR_INVALID_ARG, "chain stage buffers do not fit in shared memory");
-    if (!smem_hist) layout_for(E, false, L);
-    else layout_for(E, true, L);
+    const uint32_t cj = cap_of(lam_j), cl = cap_of(lam_l);
+    uint32_t off = 0;
+    auto add = [&](int c, size_t es, int coll, uint32_t cap) {
+        ColSpec& cs = L.col[c];
+        cs.base = nullptr;
+        cs.es = static_cast<uint32_t>(es);
+        cs.coll = static_cast<uint32_t>(coll);
+        cs.cap = static_cast<uint32_t>((cap * es + 32 + 15) & ~size_t(15));
+        cs.soff = off;
+        off += cs.cap;
+    };
+    add(J_PT, kes, 0, cj);
+    add(J_ETA, kes, 0, cj);
+    add(J_PHI, kes, 0, cj);
+    add(J_MASS, kes, 0, cj);
+    add(J_BTAG, bes, 0, cj);
+    add(M_PT, kes, 1, cl);
+    add(M_ETA, kes, 1, cl);
+    add(M_PHI, kes, 1, cl);
+    add(M_ISO, 4, 1, cl);
+    add(M_TIGHT, 1, 1, cl);
+    add(E_PT, kes, 2, cl);
+    add(E_ETA, kes, 2, cl);
+    add(E_PHI, kes, 2, cl);
+    add(E_ISO, 4, 2, cl);
+    add(E_TIGHT, 1, 2, cl);
+    auto up = [](size_t x) { return static_cast<uint32_t>((x + 127) & ~size_t(127)); };
+    L.stage_bytes = up(kHdr + off);
+    size_t at = 2 * static_cast<size_t>(L.stage_bytes);
+    L.bars = static_cast<uint32_t>(at);
+    at += 32 + 48 + 16;   // four mbarriers, spans of the next tile
+    L.edges = static_cast<uint32_t>(at);
+    at += static_cast<size_t>((P.n_edges + 3) & ~3) * 4;
+    L.queue = static_cast<uint32_t>(at);
+    at += static_cast<size_t>(E) * R_WORDS * 4;
+    L.acc_words = static_cast<int>(cj / 32 + 2);
+    L.acc = static_cast<uint32_t>(at);
+    at += static_cast<size_t>(E / 32) * L.acc_words * 4;
+    L.tri = static_cast<uint32_t>(at);
+    at += 256;
+    at = (at + 15) & ~size_t(15);
+    L.hist = static_cast<uint32_t>(at);
+    const size_t nbins = static_cast<size_t>(P.n_var) * P.total_bins;
+    if (hmode == H_SMEM) at += nbins * (8 + 8 + 4);
+    if (hmode == H_CLUSTER) {
+        L.hist_slice = static_cast<int>((nbins + cluster - 1) / cluster);
+        at += static_cast<size_t>(L.hist_slice) * (8 + 8 + 4);
+    }
+    L.total = static_cast<uint32_t>((at + 15) & ~size_t(15));
+    return L.total <= static_cast<size_t>(device_info().smem_optin);
+}
 
-    LaunchArgs a;
-    a.layout = L;
-    a.P = &P;
-    a.C = C;
-    a.joff = b->jet_offsets;
-    a.moff = b->mu_offsets;
-    a.eoff = b->el_offsets;
-    a.offsets_type = b->offsets_type;
-    a.btag_type = b->btag_type;
-    a.n = n;
-    a.out = o;
-    a.debug = debug;
-    a.smem_hist = smem_hist;
-    a.block = E;
-    a.grid = g_tuning.grid;
-    a.stream = s;
-    switch (b->kin_type) {
+hepacc_status dispatch(hepacc_dtype kin, bool batched, const LaunchArgs& a) {
+    if (batched) {
+        switch (kin) {
+            case HEPACC_F32: return run_batched_f32(a);
+            case HEPACC_F16: return run_batched_f16(a);
+            default: return run_batched_bf16(a);
+        }
+    }
+    switch (kin) {
         case HEPACC_F32: return run_f32(a);
         case HEPACC_F16: return run_f16(a);
         default: return run_bf16(a);
     }
 }
+
+}  // namespace
+}  // namespace chain
+}  // namespace hepacc
+
+using namespace hepacc;
+using namespace hepacc::chain;
+
+extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hepacc_chain_config* cfg,
+                                          const hepacc_chain_outputs* out, hepacc_stream stream) {
+    if (!b || !cfg || !out) return fail(HEPACC_ERR_INVALID_ARG, "batch, config and outputs are required");
+    ChainParams P;
+    hepacc_status st = make_params(cfg, P);
+    if (st != HEPACC_OK) return st;
+    if (!out->counts || !out->sumw) return fail(HEPACC_ERR_INVALID_ARG, "counts and sumw are required");
+    st = check_batch(b);
+    if (st != HEPACC_OK) return st;
+    if (b->n_events == 0) return HEPACC_OK;
+    BatchDesc B;
+    std::memset(&B, 0, sizeof B);
+    B.n_samples = 1;
+    make_sample(b, out, B.s[0]);
+
+    // the largest block (tile) whose layout fits, with block-private
+    // histograms when they fit, else with global ones
+    const double lam_j = b->jets_per_event > 0 ? b->jets_per_event : 6.0;
+    const double lam_l = b->leptons_per_event > 0 ? b->leptons_per_event : 1.5;
+    const size_t kes = dtype_size(b->kin_type), bes = dtype_size(b->btag_type);
+    Layout L;
+    int E = 0, hmode = H_SMEM;
+    for (int e = kMaxThreads; e >= 128 && E == 0; e -= 32)
+        if (layout_for(e, H_SMEM, 1, lam_j, lam_l, kes, bes, P, L)) E = e;
+    if (E == 0) {
+        hmode = H_GLOBAL;
+        for (int e = kMaxThreads; e >= 32 && E == 0; e -= 32)
+            if (layout_for(e, H_GLOBAL, 1, lam_j, lam_l, kes, bes, P, L)) E = e;
+    }
+    if (E == 0) return fail(HEPACC_ERR_INVALID_ARG, "chain stage buffers do not fit in shared memory");
+
+    LaunchArgs a;
+    a.layout = L;
+    a.P = &P;
+    a.B = &B;
+    a.offsets_type = b->offsets_type;
+    a.btag_type = b->btag_type;
+    a.debug = has_per_event(out);
+    a.hmode = hmode;
+    a.block = E;
+    a.cluster = 1;
+    a.grid = 0;
+    a.max_tiles = (b->n_events + E - 1) / E;
+    a.stream = reinterpret_cast<cudaStream_t>(stream);
+    return dispatch(b->kin_type, false, a);
+}
+
+// ---------------------------------------------------------------------------
+// Batched plans
+// ---------------------------------------------------------------------------
+
+struct hepacc_plan {
+    ChainParams P;
+    std::vector<BatchDesc> launches;   // up to kMaxSamples samples each
+    std::vector<hepacc_chain_outputs> outs;
+    hepacc_dtype kin, btag;
+    int64_t max_events;
+    int hmode, block, cluster;         // the chosen configuration
+    Layout L;
+    float tuned_ms;
+    int n_candidates;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+hepacc_status plan_launch(const hepacc_plan* p, cudaStream_t s) {
+    for (const BatchDesc& B : p->launches) {
+        LaunchArgs a;
+        a.layout = p->L;
+        a.P = &p->P;
+        a.B = &B;
+        a.offsets_type = HEPACC_I64;
+        a.btag_type = p->btag;
+        a.debug = false;
+        a.hmode = p->hmode;
+        a.block = p->block;
+        a.cluster = p->cluster;
+        a.grid = 0;
+        a.max_tiles = std::max<int64_t>(1, (p->max_events + p->block - 1) / p->block);
+        a.stream = s;
+        const hepacc_status st = dispatch(p->kin, true, a);
+        if (st != HEPACC_OK) return st;
+    }
+    return HEPACC_OK;
+}
+
+hepacc_status zero_outputs(const hepacc_plan* p, cudaStream_t s) {
+    const size_t nb = static_cast<size_t>(p->P.n_var) * p->P.total_bins;
+    for (const hepacc_chain_outputs& o : p->outs) {
+        cudaError_t e = cudaMemsetAsync(o.counts, 0, nb * sizeof(uint64_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(o.sumw, 0, nb * sizeof(double), s);
+        if (e == cudaSuccess && o.sumw2) e = cudaMemsetAsync(o.sumw2, 0, nb * sizeof(double), s);
+        if (e != cudaSuccess) return cuda_fail(e, "clearing plan outputs");
+    }
+    return HEPACC_OK;
+}
+
+struct Candidate {
+    int hmode, cluster, block;
+    Layout L;
+};
+
+// Times every candidate (one warm-up run, two timed) on the plan's samples
+// and returns the index of the fastest, -1 if none ran.
+int autotune(hepacc_plan* p, const std::vector<Candidate>& cands, cudaStream_t s, float& best_ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return -1;
+    }
+    int pick = -1;
+    best_ms = -1.0f;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        p->hmode = cands[i].hmode;
+        p->cluster = cands[i].cluster;
+        p->block = cands[i].block;
+        p->L = cands[i].L;
+        if (plan_launch(p, s) != HEPACC_OK) continue;
+        cudaEventRecord(e0, s);
+        const bool ok = plan_launch(p, s) == HEPACC_OK && plan_launch(p, s) == HEPACC_OK;
+        cudaEventRecord(e1, s);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            (best_ms < 0.0f || ms < best_ms)) {
+            best_ms = ms;
+            pick = static_cast<int>(i);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (pick >= 0) best_ms *= 0.5f;
+    return pick;
+}
+
+hepacc_status capture(hepacc_plan* p) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    hepacc_status st = HEPACC_OK;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        st = plan_launch(p, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+        if (st == HEPACC_OK && e2 != cudaSuccess) st = cuda_fail(e2, "graph capture");
+    } else {
+        st = cuda_fail(e, "begin capture");
+    }
+    if (st == HEPACC_OK) {
+        e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "graph instantiate");
+    }
+    cudaStreamDestroy(cs);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_samples, const hepacc_event_batch* samples,
+                                 const hepacc_chain_outputs* outputs, int32_t flags, hepacc_stream stream,
+                                 hepacc_plan** plan) {
+    if (!plan) return fail(HEPACC_ERR_INVALID_ARG, "plan is required");
+    *plan = nullptr;
+    if (!cfg) return fail(HEPACC_ERR_INVALID_ARG, "config is required");
+    if (n_samples < 1 || !samples || !outputs) return fail(HEPACC_ERR_INVALID_ARG, "need at least one sample and its outputs");
+    const int hist_flags = HEPACC_PLAN_HIST_BLOCK | HEPACC_PLAN_HIST_CLUSTER8 | HEPACC_PLAN_HIST_CLUSTER16 |
+                           HEPACC_PLAN_HIST_GLOBAL;
+    if (flags & ~(HEPACC_PLAN_AUTOTUNE | HEPACC_PLAN_GRAPH | hist_flags))
+        return fail(HEPACC_ERR_INVALID_ARG, "unknown plan flags");
+    const int allowed = (flags & hist_flags) ? (flags & hist_flags) : hist_flags;
+    hepacc_plan* p = new (std::nothrow) hepacc_plan();
+    if (!p) return fail(HEPACC_ERR_OOM, "plan allocation");
+    auto drop = [&](hepacc_status st) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        delete p;
+        return st;
+    };
+    hepacc_status st = make_params(cfg, p->P);
+    if (st != HEPACC_OK) return drop(st);
+    double jets = 0, leps = 0, events = 0;
+    p->max_events = 0;
+    for (int i = 0; i < n_samples; ++i) {
+        const hepacc_event_batch& b = samples[i];
+        const hepacc_chain_outputs& o = outputs[i];
+        st = check_batch(&b);
+        if (st != HEPACC_OK) return drop(st);
+        if (!o.counts || !o.sumw) return drop(fail(HEPACC_ERR_INVALID_ARG, "sample %d: counts and sumw are required", i));
+        if (has_per_event(&o)) return drop(fail(HEPACC_ERR_INVALID_ARG, "plans write no per-event outputs"));
+        if (b.offsets_type != HEPACC_I64) return drop(fail(HEPACC_ERR_DTYPE, "plans need I64 offsets"));
+        if (b.kin_type != samples[0].kin_type || b.btag_type != samples[0].btag_type)
+            return drop(fail(HEPACC_ERR_DTYPE, "all samples of a plan share their column types"));
+        if ((b.kin_type == HEPACC_F32) != (b.btag_type == HEPACC_F32))
+            return drop(fail(HEPACC_ERR_DTYPE, "plans take F32 btag with F32 kinematics, F16 btag with half kinematics"));
+        const double n = static_cast<double>(b.n_events);
+        jets += (b.jets_per_event > 0 ? b.jets_per_event : 6.0) * n;
+        leps += (b.leptons_per_event > 0 ? b.leptons_per_event : 1.5) * n;
+        events += n;
+        p->max_events = std::max<int64_t>(p->max_events, b.n_events);
+    }
+    p->kin = samples[0].kin_type;
+    p->btag = samples[0].btag_type;
+    const double lam_j = events > 0 ? jets / events : 6.0;
+    const double lam_l = events > 0 ? leps / events : 1.5;
+    p->outs.assign(outputs, outputs + n_samples);
+    for (int i0 = 0; i0 < n_samples; i0 += kMaxSamples) {
+        BatchDesc B;
+        std::memset(&B, 0, sizeof B);
+        B.n_samples = std::min(kMaxSamples, n_samples - i0);
+        for (int j = 0; j < B.n_samples; ++j) make_sample(&samples[i0 + j], &outputs[i0 + j], B.s[j]);
+        p->launches.push_back(B);
+    }
+
+    // candidates: histograms in block shared memory, spread over clusters of
+    // 8 or 16 blocks, or in global memory; each with the largest block that
+    // fits
+    const size_t kes = dtype_size(p->kin), bes = dtype_size(p->btag);
+    std::vector<Candidate> cands;
+    const int modes[4][3] = {{H_SMEM, 1, HEPACC_PLAN_HIST_BLOCK},
+                             {H_CLUSTER, 8, HEPACC_PLAN_HIST_CLUSTER8},
+                             {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16},
+                             {H_GLOBAL, 1, HEPACC_PLAN_HIST_GLOBAL}};
+    for (const auto& m : modes)
+        for (int e = kMaxThreads; e >= 128 && (allowed & m[2]); e -= 32) {
+            Candidate c;
+            if (layout_for(e, m[0], m[1], lam_j, lam_l, kes, bes, p->P, c.L)) {
+                c.hmode = m[0];
+                c.cluster = m[1];
+                c.block = e;
+                cands.push_back(c);
+                break;
+            }
+        }
+    if (cands.empty()) return drop(fail(HEPACC_ERR_INVALID_ARG, "no chain layout fits in shared memory"));
+    p->n_candidates = static_cast<int>(cands.size());
+    p->tuned_ms = -1.0f;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int pick = 0;
+    if (flags & HEPACC_PLAN_AUTOTUNE) {
+        pick = autotune(p, cands, s, p->tuned_ms);
+        cudaGetLastError();   // failures of rejected candidates
+        if (pick < 0) return drop(fail(HEPACC_ERR_CUDA, "no candidate chain configuration ran"));
+        st = zero_outputs(p, s);
+        if (st == HEPACC_OK) {
+            const cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_fail(e, "autotune");
+        }
+        if (st != HEPACC_OK) return drop(st);
+    }
+    p->hmode = cands[pick].hmode;
+    p->cluster = cands[pick].cluster;
+    p->block = cands[pick].block;
+    p->L = cands[pick].L;
+    if (flags & HEPACC_PLAN_GRAPH) {
+        st = capture(p);
+        if (st != HEPACC_OK) return drop(st);
+    }
+    *plan = p;
+    return HEPACC_OK;
+}
+
+hepacc_status hepacc_plan_run(hepacc_plan* p, hepacc_stream stream) {
+    if (!p) return fail(HEPACC_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->exec) {
+        const cudaError_t e = cudaGraphLaunch(p->exec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        return HEPACC_OK;
+    }
+    return plan_launch(p, s);
+}
+
+hepacc_status hepacc_plan_describe(const hepacc_plan* p, char* buf, int32_t len) {
+    if (!p || !buf || len < 1) return fail(HEPACC_ERR_INVALID_ARG, "plan and buffer are required");
+    const char* mode = p->hmode == H_SMEM ? "block" : (p->hmode == H_CLUSTER ? "cluster" : "global");
+    snprintf(buf, static_cast<size_t>(len),
+             "{\"histograms\": \"%s\", \"cluster\": %d, \"block\": %d, \"smem_bytes\": %u, \"launches\": %d, "
+             "\"graph\": %s, \"candidates\": %d, \"tuned_ms\": %.4f}",
+             mode, p->cluster, p->block, p->L.total, static_cast<int>(p->launches.size()),
+             p->exec ? "true" : "false", p->n_candidates, static_cast<double>(p->tuned_ms));
+    return HEPACC_OK;
+}
+
+void hepacc_plan_destroy(hepacc_plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    delete p;
+}
+
+}  // extern "C"

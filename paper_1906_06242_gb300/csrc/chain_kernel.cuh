@@ -1,6 +1,7 @@
 // The fused benchmark chain of Section IV of arXiv:1906.06242: kernel
-// templates shared by the per-type translation units (chain_f32.cu,
-// chain_bf16.cu, chain_f16.cu) and the host entry point (chain.cu).
+// templates shared by the per-type translation units (chain_<type>.cu for
+// single-sample launches, chain_batched_<type>.cu for many samples per
+// launch) and the host side (chain.cu).
 //
 // One kernel, persistent blocks; a block works on tiles of E = blockDim.x
 // consecutive events (thread = event):
@@ -19,10 +20,14 @@
 //    queue;
 //  * masses (thread = queued pair, 32 at a time per warp): pair and triplet
 //    invariant masses and the 20 variables, pure arithmetic;
-//  * fill: per histogram, lanes bin the warp's queued values, lanes that hit
-//    the same bin are merged, one shared-memory atomic per bin (or a global
-//    one when n_var histogram copies do not fit in shared memory); blocks
-//    add their histograms to the output at exit.
+//  * fill: lane h bins variable h of every queued entry (no two lanes of a
+//    warp touch one bin) into the histograms of the placement: block-private
+//    shared memory, shared memory spread over a thread-block cluster
+//    (distributed shared memory reductions into the block that owns the
+//    bin) or global memory; shared-memory histograms go to the outputs when
+//    the block is done with a sample.
+// Batched launches walk through up to kMaxSamples samples in turn, each with
+// its own columns and outputs, without a grid-wide barrier between them.
 #pragma once
 
 #include <algorithm>
@@ -40,7 +45,7 @@ constexpr int NC = 15;            // staged columns
 constexpr int kNV = HEPACC_CHAIN_NVARS;
 constexpr int kQ = kNV + 1;       // fill entry: 20 variables + variation
 constexpr int kScratch = 10;      // selected jets ranked from a queue slot (2 x 10 words of it)
-constexpr int kMaxThreads = 384;
+constexpr int kMaxThreads = 320;
 constexpr int kHdr = 96;          // stage header: spans, staged flag, column offsets
 
 enum : int { J_PT = 0, J_ETA, J_PHI, J_MASS, J_BTAG, M_PT, M_ETA, M_PHI, M_ISO, M_TIGHT, E_PT, E_ETA, E_PHI, E_ISO, E_TIGHT };
@@ -70,16 +75,45 @@ struct ChainOut {
     float* ev_vars;
 };
 
-struct ChainCols {
-    const void *jet_pt, *jet_eta, *jet_phi, *jet_mass, *jet_btag;
-    const void *mu_pt, *mu_eta, *mu_phi;
-    const float *mu_iso;
-    const uint8_t *mu_tight;
-    const void *el_pt, *el_eta, *el_phi;
-    const float *el_iso;
-    const uint8_t *el_tight;
-    const float *weight;
+// One sample of a launch: column bases (staged-column order), offsets,
+// weights and its outputs.
+constexpr int kMaxSamples = 16;
+struct SampleDesc {
+    const void* col[NC];
+    const float* weight;
+    const void* off[3];
+    int64_t n;
+    ChainOut out;
 };
+struct BatchDesc {
+    int n_samples;
+    SampleDesc s[kMaxSamples];
+};
+
+// Histogram placement: block-private shared memory, global memory, or
+// spread over the shared memory of a thread-block cluster (each block owns
+// a contiguous slice of the bins, updated through distributed shared memory).
+enum : int { H_SMEM = 0, H_GLOBAL = 1, H_CLUSTER = 2 };
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void red_cluster_u32(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_cluster_f64(uint32_t addr, double v) {
+    asm volatile("red.shared::cluster.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 // Shared-memory layout of a block (byte offsets into dynamic shared memory).
 struct Layout {
@@ -91,7 +125,8 @@ struct Layout {
     uint32_t acc;          // per warp acc_words words of jet acceptance flags
     int acc_words;
     uint32_t tri;          // triplet table (uint16 per triplet, colex order)
-    uint32_t hist;         // block-private histograms (SMEM_HIST)
+    uint32_t hist;         // histograms (H_SMEM: all bins, H_CLUSTER: this block's slice)
+    int hist_slice;        // H_CLUSTER: bins per block
     uint32_t total;
 };
 
@@ -110,30 +145,6 @@ __device__ __forceinline__ float gload(const void* p, int64_t i) {
     return Elem<T>::f(static_cast<const T*>(p)[i]);
 }
 
-// Jet acceptance straight from global memory (|eta| and Delta R to every
-// selected lepton of event e); used for jets past the 64 cached flags.
-template <typename KT, typename OffT>
-__device__ bool jet_ok_global(const ChainParams& P, const ChainCols& C, const OffT* moff, const OffT* eoff,
-                              int64_t e, int64_t i) {
-    const float eta = gload<KT>(C.jet_eta, i);
-    if (!(fabsf(eta) < P.jet_abseta_max)) return false;
-    const float phi = gload<KT>(C.jet_phi, i);
-    for (int f = 0; f < 2; ++f) {
-        const OffT* off = f == 0 ? moff : eoff;
-        const void* pt = f == 0 ? C.mu_pt : C.el_pt;
-        const void* le = f == 0 ? C.mu_eta : C.el_eta;
-        const void* lp = f == 0 ? C.mu_phi : C.el_phi;
-        const float* iso = f == 0 ? C.mu_iso : C.el_iso;
-        const uint8_t* tight = f == 0 ? C.mu_tight : C.el_tight;
-        for (int64_t l = ldoff(off, e); l < ldoff(off, e + 1); ++l) {
-            const float p = gload<KT>(pt, l), x = gload<KT>(le, l);
-            const bool sel = p > P.lep_pt_min && fabsf(x) < P.lep_abseta_max && tight[l] != 0 && iso[l] < P.lep_iso_max;
-            if (sel && dr2_f32(eta, phi, x, gload<KT>(lp, l)) < P.dr2_cut) return false;
-        }
-    }
-    return true;
-}
-
 // Column access for the selection phase.
 struct StagedCols {
     uint32_t off[NC];      // byte offset of the tile's first element of each column in shared memory
@@ -143,11 +154,12 @@ struct StagedCols {
     }
 };
 struct DirectCols {
-    const Layout* L;       // column bases (kernel parameters)
+    const Layout* L;       // column element sizes and collections
+    const void* const* base;   // column bases of the sample
     int64_t S[3];          // the tile's first element per collection
     template <typename T>
     __device__ __forceinline__ T ld(int c, int r) const {
-        return reinterpret_cast<const T*>(L->col[c].base)[S[L->col[c].coll] + r];
+        return reinterpret_cast<const T*>(base[c])[S[L->col[c].coll] + r];
     }
 };
 
@@ -158,11 +170,10 @@ __device__ __forceinline__ void put4(uint32_t* q, float a, float b, float c, flo
     q[3] = __float_as_uint(d);
 }
 
-template <typename KT, typename BT, typename OffT, bool DEBUG, bool SMEM_HIST>
+template <typename KT, typename BT, typename OffT, bool DEBUG, int HMODE, bool MULTI>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant__ Layout L,
-                                                          const __grid_constant__ ChainParams P, ChainCols C,
-                                                          const OffT* joff, const OffT* moff, const OffT* eoff,
-                                                          int64_t n, ChainOut out) {
+                                                          const __grid_constant__ ChainParams P,
+                                                          const __grid_constant__ BatchDesc B) {
     unsigned char* smem = g_dyn_smem;
     const int tid = threadIdx.x;
     const int E = blockDim.x;
@@ -173,9 +184,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
     float* s_edges = reinterpret_cast<float*>(smem + L.edges);
     uint32_t* my_q = reinterpret_cast<uint32_t*>(smem + L.queue) + warp * 32 * R_WORDS;
     const int hist_n = P.n_var * P.total_bins;
+    const int hist_local = HMODE == H_SMEM ? hist_n : (HMODE == H_CLUSTER ? L.hist_slice : 0);
     double* s_w = reinterpret_cast<double*>(smem + L.hist);
-    double* s_w2 = s_w + (SMEM_HIST ? hist_n : 0);
-    unsigned int* s_c = reinterpret_cast<unsigned int*>(s_w2 + (SMEM_HIST ? hist_n : 0));
+    double* s_w2 = s_w + hist_local;
+    unsigned int* s_c = reinterpret_cast<unsigned int*>(s_w2 + hist_local);
+    const uint32_t my_rank = HMODE == H_CLUSTER ? cluster_ctarank() : 0u;
     uint16_t* s_tri = reinterpret_cast<uint16_t*>(smem + L.tri);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
     const uint32_t full[2] = {smem_addr(bars), smem_addr(bars + 1)};
@@ -191,12 +204,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             for (int b2 = 1; b2 < c; ++b2)
                 for (int a = 0; a < b2; ++a) s_tri[t++] = static_cast<uint16_t>(a | (b2 << 4) | (c << 8));
     }
-    if (SMEM_HIST) {
-        for (int i = tid; i < hist_n; i += E) {
-            s_w[i] = 0.0;
-            s_w2[i] = 0.0;
-            s_c[i] = 0u;
-        }
+    for (int i = tid; i < hist_local; i += E) {
+        s_w[i] = 0.0;
+        s_w2[i] = 0.0;
+        s_c[i] = 0u;
     }
     if (tid == 0) {
         mbar_init(full[0], 1);
@@ -206,10 +217,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         fence_mbar_init();
     }
     __syncthreads();
+    if (HMODE == H_CLUSTER) cluster_sync_all();
 
-    const OffT* const offs[3] = {joff, moff, eoff};
-    const int64_t ntiles = (n + E - 1) / E;
+    // the sample being processed (set at the top of the sample loop; always
+    // 0 for single-sample launches)
+    int si = 0;
+    const OffT* offs[3] = {nullptr, nullptr, nullptr};
+    int64_t n = 0;
+    int64_t ntiles = 0;
     const int64_t grid = gridDim.x;
+    const float* weight = nullptr;
 
     // thread 0: first and last element of every collection in tile tt
     auto load_span = [&](int64_t tt, int64_t (&S)[3], int64_t (&T)[3]) {
@@ -231,8 +248,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const ColSpec& cs = L.col[c];
-            const uintptr_t a = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
-            const uintptr_t z = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
+            const uintptr_t cb = reinterpret_cast<uintptr_t>(B.s[si].col[c]);
+            const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
+            const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
             const uintptr_t bytes = T[cs.coll] > S[cs.coll] ? ((z + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)) : 0;
             if (bytes > cs.cap) fits = false;
             total += static_cast<uint32_t>(bytes);
@@ -249,8 +267,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             for (int c = 0; c < NC; ++c) {
                 const ColSpec& cs = L.col[c];
                 if (T[cs.coll] <= S[cs.coll]) continue;
-                const uintptr_t a = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
-                const uintptr_t z = reinterpret_cast<uintptr_t>(cs.base) + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
+                const uintptr_t cb = reinterpret_cast<uintptr_t>(B.s[si].col[c]);
+                const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
+                const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
                 const uintptr_t a16 = a & ~uintptr_t(15);
                 const uint32_t bytes = static_cast<uint32_t>(((z + 15) & ~uintptr_t(15)) - a16);
                 bulk_g2s(smem0 + b * L.stage_bytes + kHdr + cs.soff, reinterpret_cast<const void*>(a16), bytes, full[b]);
@@ -262,6 +281,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
 
     // Masses and fill for this warp's queued records [0, m) (warp-uniform).
     auto flush = [&](int m) {
+        const ChainOut& out = B.s[si].out;
         const uint32_t* r = my_q + lane * R_WORDS;   // this lane's record
         const bool have = lane < m;
         float var[kNV];
@@ -364,10 +384,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                 if (bin < 0) continue;
                 const int at = static_cast<int>(kk) * P.total_bins + boff + bin;
                 const double wd = static_cast<double>(__uint_as_float(q[19]));
-                if (SMEM_HIST) {
+                if (HMODE == H_SMEM) {
                     atomicAdd(&s_c[at], 1u);
                     atomicAdd(&s_w[at], wd);
                     if (out.sumw2) atomicAdd(&s_w2[at], wd * wd);
+                } else if (HMODE == H_CLUSTER) {
+                    const uint32_t rk = static_cast<uint32_t>(at) / static_cast<uint32_t>(L.hist_slice);
+                    const int loc = at - static_cast<int>(rk) * L.hist_slice;
+                    red_cluster_u32(map_to_rank(smem_addr(s_c + loc), rk), 1u);
+                    red_cluster_f64(map_to_rank(smem_addr(s_w + loc), rk), wd);
+                    if (out.sumw2) red_cluster_f64(map_to_rank(smem_addr(s_w2 + loc), rk), wd * wd);
                 } else {
                     atomicAdd(&out.counts[at], 1ull);
                     atomicAdd(&out.sumw[at], wd);
@@ -379,19 +405,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
     };
 
     int qcount = 0;
-    int64_t tile = blockIdx.x;
     int64_t (&S1)[3] = *reinterpret_cast<int64_t(*)[3]>(smem + L.bars + 32);   // thread 0: spans of the next tile
     int64_t (&T1)[3] = *reinterpret_cast<int64_t(*)[3]>(smem + L.bars + 56);
-    int64_t cs_[3] = {0, 0, 0}, ct_[3] = {0, 0, 0};
     uint32_t fpar[2] = {0u, 0u};
     uint32_t uses[2] = {0u, 0u};   // thread 0: copies issued into each stage
     int b = 0;
+    bool stop = false;   // a bounded wait gave up: skip the remaining work, keep the barriers
+    for (int sl = 0; sl < (MULTI ? B.n_samples : 1); ++sl) {
+    si = MULTI ? sl : 0;
+    offs[0] = static_cast<const OffT*>(B.s[si].off[0]);
+    offs[1] = static_cast<const OffT*>(B.s[si].off[1]);
+    offs[2] = static_cast<const OffT*>(B.s[si].off[2]);
+    n = B.s[si].n;
+    ntiles = (n + E - 1) / E;
+    weight = B.s[si].weight;
+    int64_t tile = stop ? ntiles : blockIdx.x;
+    int64_t cs_[3] = {0, 0, 0}, ct_[3] = {0, 0, 0};
     if (tile < ntiles) {
         if (tid == 0) {
             int64_t S0[3], T0[3];
             load_span(tile, S0, T0);
-            issue(0, S0, T0);
-            uses[0] = 1;
+            // the stage is free once every warp released its last use
+            bool ok = true;
+            if (uses[b] > 0) ok = mbar_wait_bounded(empty[b], (uses[b] - 1) & 1u);
+            if (ok) {
+                issue(b, S0, T0);
+                ++uses[b];
+            }
             if (tile + grid < ntiles) load_span(tile + grid, S1, T1);
         }
         const int64_t e = tile * E + tid;
@@ -425,7 +465,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                 nt_[c] = ldoff(offs[c], ehi);
             }
         }
-        if (!mbar_wait_bounded(full[b], fpar[b])) break;   // error word set; this warp stops
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(full[b], fpar[b]))) {   // error word set; this warp stops
+            stop = true;
+            break;
+        }
         fpar[b] ^= 1u;
 
         const unsigned char* st = smem + b * L.stage_bytes;
@@ -443,6 +486,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         StagedCols sc;
         DirectCols dc;
         dc.L = &L;
+        dc.base = B.s[si].col;
 #pragma unroll
         for (int c = 0; c < 3; ++c) dc.S[c] = hdr[c];
         if (staged) {
@@ -517,7 +561,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             else
                 lep_vals(dc);
         }
-        if (DEBUG && valid && out.ev_nlep) out.ev_nlep[e] = nlep;
+        if (DEBUG && valid && B.s[si].out.ev_nlep) B.s[si].out.ev_nlep[e] = nlep;
         // without per-event outputs only single-lepton events can pass
         const bool active = valid && (DEBUG || nlep == 1);
         const unsigned amask = __ballot_sync(0xffffffffu, active);
@@ -698,7 +742,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                  Elem<KT>::f(T.template ld<KT>(J_PHI, i)), Elem<KT>::f(T.template ld<KT>(J_MASS, i)));
         };
 
-        const float w = valid ? C.weight[e] : 0.0f;
+        const float w = valid ? weight[e] : 0.0f;
         for (int k = 0; k < P.n_var; ++k) {
             const float s = P.scales[k];
             int njet = 0, nbj = 0;
@@ -831,31 +875,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         b ^= 1;
     }
     if (qcount > 0) flush(qcount);
+    qcount = 0;
 
-    if (SMEM_HIST) {
-        __syncthreads();
-        for (int i = tid; i < hist_n; i += E) {
+    // the sample's histograms: block-private or cluster-slice copies go to
+    // the sample's outputs and are cleared for the next sample
+    if (HMODE != H_GLOBAL) {
+        const ChainOut& out = B.s[si].out;
+        if (HMODE == H_CLUSTER)
+            cluster_sync_all();
+        else
+            __syncthreads();
+        const int first = HMODE == H_CLUSTER ? static_cast<int>(my_rank) * L.hist_slice : 0;
+        for (int i = tid; i < hist_local; i += E) {
+            const int g = first + i;
             const unsigned c = s_c[i];
-            if (c == 0u) continue;
-            atomicAdd(&out.counts[i], static_cast<unsigned long long>(c));
-            atomicAdd(&out.sumw[i], s_w[i]);
-            if (out.sumw2) atomicAdd(&out.sumw2[i], s_w2[i]);
+            if (c != 0u && g < hist_n) {
+                atomicAdd(&out.counts[g], static_cast<unsigned long long>(c));
+                atomicAdd(&out.sumw[g], s_w[i]);
+                if (out.sumw2) atomicAdd(&out.sumw2[g], s_w2[i]);
+            }
+            s_c[i] = 0u;
+            s_w[i] = 0.0;
+            s_w2[i] = 0.0;
         }
+        if (HMODE == H_CLUSTER)
+            cluster_sync_all();
+        else
+            __syncthreads();
+    }
     }
 }
 
-// Launch parameters prepared by hepacc_run_chain for the typed launchers.
+// Launch parameters prepared by the host entry points for the typed launchers.
 struct LaunchArgs {
     Layout layout;
     const ChainParams* P;
-    ChainCols C;
-    const void *joff, *moff, *eoff;
+    const BatchDesc* B;
     hepacc_dtype offsets_type, btag_type;
-    int64_t n;
-    ChainOut out;
-    bool debug, smem_hist;
+    bool debug;
+    int hmode;
     int block;
-    int grid;            // 0 = one block per SM
+    int cluster;         // blocks per cluster (H_CLUSTER)
+    int grid;            // 0 = as many resident blocks (clusters) as fit
+    int64_t max_tiles;   // most tiles of any sample (caps the grid)
     cudaStream_t stream;
 };
 
@@ -870,10 +932,10 @@ inline Cache& cache() {
     return c;
 }
 
-template <typename K, typename... A>
-hepacc_status launch_chain(K kernel, int block, size_t smem, int64_t n, cudaStream_t stream, int grid_override,
-                           A... args) {
+template <typename K>
+hepacc_status launch_chain(K kernel, const LaunchArgs& a) {
     const DeviceInfo di = device_info();
+    const size_t smem = a.layout.total;
     if (smem > static_cast<size_t>(di.smem_optin)) return fail(HEPACC_ERR_INVALID_ARG, "chain shared memory too large");
     {
         std::lock_guard<std::mutex> g(cache().mu);
@@ -881,17 +943,45 @@ hepacc_status launch_chain(K kernel, int block, size_t smem, int64_t n, cudaStre
         if (it == cache().smem_set.end() || it->second < static_cast<int>(smem)) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            if (a.hmode == H_CLUSTER) {
+                e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                if (e != cudaSuccess) return cuda_fail(e, "cluster size attribute");
+            }
             cache().smem_set[reinterpret_cast<const void*>(kernel)] = static_cast<int>(smem);
         }
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if (per_sm < 1) return fail(HEPACC_ERR_INVALID_ARG, "chain kernel does not fit on an SM");
-    const int64_t ntiles = (n + block - 1) / block;
-    int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ntiles, static_cast<int64_t>(per_sm) * di.sms)));
-    if (grid_override > 0) grid = grid_override;
-    kernel<<<grid, block, smem, stream>>>(args...);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(a.block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = a.stream;
+    int grid = 0;
+    if (a.hmode == H_CLUSTER) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = a.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(a.cluster * di.sms, 1, 1);
+        int nclusters = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+        if (nclusters < 1) return fail(HEPACC_ERR_INVALID_ARG, "chain clusters of %d blocks do not fit", a.cluster);
+        grid = nclusters * a.cluster;
+        if (a.grid > 0) grid = std::min(grid, (a.grid / a.cluster) * a.cluster);
+        if (grid < a.cluster) grid = a.cluster;
+    } else {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, a.block, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        if (per_sm < 1) return fail(HEPACC_ERR_INVALID_ARG, "chain kernel does not fit on an SM");
+        grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(a.max_tiles, static_cast<int64_t>(per_sm) * di.sms)));
+        if (a.grid > 0) grid = a.grid;
+    }
+    cfg.gridDim = dim3(grid, 1, 1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, a.layout, *a.P, *a.B);
+    if (e != cudaSuccess) return cuda_fail(e, "chain launch");
     HEPACC_CHECK_LAUNCH("chain launch");
     return HEPACC_OK;
 }
@@ -901,22 +991,12 @@ hepacc_status run_typed(const LaunchArgs& a) {
     auto go = [&](auto bt, auto ot) -> hepacc_status {
         using BT = typename decltype(bt)::type;
         using O = typename decltype(ot)::type;
-        const O* jo = static_cast<const O*>(a.joff);
-        const O* mo = static_cast<const O*>(a.moff);
-        const O* eo = static_cast<const O*>(a.eoff);
-        const size_t smem = a.layout.total;
         if (a.debug) {
-            if (a.smem_hist)
-                return launch_chain(k_chain<KT, BT, O, true, true>, a.block, smem, a.n, a.stream, a.grid, a.layout,
-                                    *a.P, a.C, jo, mo, eo, a.n, a.out);
-            return launch_chain(k_chain<KT, BT, O, true, false>, a.block, smem, a.n, a.stream, a.grid, a.layout, *a.P,
-                                a.C, jo, mo, eo, a.n, a.out);
+            if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, true, H_SMEM, false>, a);
+            return launch_chain(k_chain<KT, BT, O, true, H_GLOBAL, false>, a);
         }
-        if (a.smem_hist)
-            return launch_chain(k_chain<KT, BT, O, false, true>, a.block, smem, a.n, a.stream, a.grid, a.layout, *a.P,
-                                a.C, jo, mo, eo, a.n, a.out);
-        return launch_chain(k_chain<KT, BT, O, false, false>, a.block, smem, a.n, a.stream, a.grid, a.layout, *a.P, a.C,
-                            jo, mo, eo, a.n, a.out);
+        if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, false, H_SMEM, false>, a);
+        return launch_chain(k_chain<KT, BT, O, false, H_GLOBAL, false>, a);
     };
     auto with_o = [&](auto bt) -> hepacc_status {
         if (a.offsets_type == HEPACC_I32) return go(bt, Tag<int32_t>{});
@@ -926,12 +1006,28 @@ hepacc_status run_typed(const LaunchArgs& a) {
     return with_o(Tag<__half>{});
 }
 
+// Many samples in one launch (int64 offsets; btag float32 with float32
+// kinematics, float16 with half kinematics).
+template <typename KT, typename BT>
+hepacc_status run_batched_typed(const LaunchArgs& a) {
+    if (a.offsets_type != HEPACC_I64) return fail(HEPACC_ERR_DTYPE, "batched launches need I64 offsets");
+    if (a.hmode == H_CLUSTER) return launch_chain(k_chain<KT, BT, int64_t, false, H_CLUSTER, true>, a);
+    if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, int64_t, false, H_SMEM, true>, a);
+    return launch_chain(k_chain<KT, BT, int64_t, false, H_GLOBAL, true>, a);
+}
+
 hepacc_status run_f32(const LaunchArgs& a);
 hepacc_status run_bf16(const LaunchArgs& a);
 hepacc_status run_f16(const LaunchArgs& a);
+hepacc_status run_batched_f32(const LaunchArgs& a);
+hepacc_status run_batched_bf16(const LaunchArgs& a);
+hepacc_status run_batched_f16(const LaunchArgs& a);
 unsigned int tu_error_f32(bool clear);
 unsigned int tu_error_bf16(bool clear);
 unsigned int tu_error_f16(bool clear);
+unsigned int tu_error_batched_f32(bool clear);
+unsigned int tu_error_batched_bf16(bool clear);
+unsigned int tu_error_batched_f16(bool clear);
 
 }  // namespace chain
 }  // namespace hepacc

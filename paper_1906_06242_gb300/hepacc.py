@@ -8,6 +8,7 @@ There is no CPU path: if the library cannot be loaded, calls raise.
 from __future__ import annotations
 
 import ctypes
+import json
 import math
 import os
 
@@ -63,8 +64,13 @@ def load(build_if_missing: bool = True):
                  "hepacc_get_in_offsets", "hepacc_set_in_offsets", "hepacc_select_range", "hepacc_scale",
                  "hepacc_mask_deltar", "hepacc_fill_histogram", "hepacc_pair_mass", "hepacc_max_pt_trijet",
                  "hepacc_run_chain", "hepacc_validate_offsets", "hepacc_device_error",
-                 "hepacc_selftest_wait_timeout"):
+                 "hepacc_selftest_wait_timeout", "hepacc_plan_create", "hepacc_plan_run",
+                 "hepacc_plan_describe"):
         getattr(L, name).restype = ctypes.c_int
+    L.hepacc_plan_destroy.restype = None
+    L.hepacc_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.hepacc_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.hepacc_plan_describe.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]
     _lib = L
     return L
 
@@ -446,3 +452,52 @@ def hepacc_run_chain(batch: DeviceBatch, cfg: ChainConfig, out: ChainOutputs, st
     bc, cc, oc = _structs
     _check(load().hepacc_run_chain(ctypes.byref(bc), ctypes.byref(cc), ctypes.byref(oc), _stream(stream)))
     return out
+
+
+PLAN_AUTOTUNE = 1
+PLAN_GRAPH = 2
+
+
+class Plan:
+    """A batched chain plan (``hepacc_plan_create``): samples, their outputs
+    and the launch configuration, run with :meth:`run`. Keeps the Python
+    objects whose device memory the plan points at alive."""
+
+    def __init__(self, handle, batches, outputs, cfg):
+        self._h = handle
+        self.batches = batches
+        self.outputs = outputs
+        self.cfg = cfg
+
+    def run(self, stream=None):
+        _check(load().hepacc_plan_run(self._h, _stream(stream)))
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(512)
+        _check(load().hepacc_plan_describe(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if self._h:
+            load().hepacc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hepacc_plan_create(cfg: ChainConfig, batches, outputs, flags=PLAN_AUTOTUNE | PLAN_GRAPH, stream=None) -> Plan:
+    """Plan the chain over many samples (``batches[i]`` adds to
+    ``outputs[i]``); see :class:`Plan`."""
+    if len(batches) != len(outputs) or not batches:
+        raise ValueError("one output per sample, at least one sample")
+    n = len(batches)
+    bs = (EventBatchC * n)(*[b.c_struct() for b in batches])
+    os_ = (ChainOutputsC * n)(*[o.c_struct() for o in outputs])
+    cc = cfg.c_struct()
+    h = ctypes.c_void_p()
+    _check(load().hepacc_plan_create(ctypes.byref(cc), n, bs, os_, int(flags), _stream(stream), ctypes.byref(h)))
+    return Plan(h, list(batches), list(outputs), cfg)

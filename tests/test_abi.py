@@ -64,3 +64,38 @@ def test_host_side_errors_without_gpu(lib):
     assert st == 1
     # chain: null config
     assert lib.hepacc_run_chain(None, None, None, None) == 1
+
+
+def test_plan_host_side_errors_without_gpu(lib):
+    from paper_1906_06242_gb300 import hepacc as H
+    from paper_1906_06242_gb300 import synth
+    C = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [1.0])
+    cfg = C.c_struct()
+
+    def batch(offsets=H.I64, kin=H.F32, btag=H.F32):
+        b = H.EventBatchC()
+        b.n_events = 10
+        b.offsets_type, b.kin_type, b.btag_type = offsets, kin, btag
+        for f in H.COLUMNS + ("jet_offsets", "mu_offsets", "el_offsets", "weight"):
+            setattr(b, f, 16)
+        return b
+
+    out = H.ChainOutputsC()
+    out.counts = out.sumw = 16
+    plan = ctypes.c_void_p()
+
+    def create(b, o, flags=0, n=1, p=ctypes.byref(plan)):
+        return lib.hepacc_plan_create(ctypes.byref(cfg), n, ctypes.byref(b), ctypes.byref(o), flags, None, p)
+
+    assert create(batch(), out, p=None) == 1                 # no plan pointer
+    assert create(batch(), out, n=0) == 1                    # no samples
+    assert create(batch(), out, flags=1 << 10) == 1          # unknown flag
+    per_event = H.ChainOutputsC()
+    per_event.counts = per_event.sumw = per_event.ev_pass = 16
+    assert create(batch(), per_event) == 1                   # plans write no per-event outputs
+    assert create(batch(offsets=H.I32), out) == 2            # int64 offsets only
+    assert create(batch(kin=H.BF16, btag=H.F32), out) == 2   # half kinematics take half btag
+    no_counts = H.ChainOutputsC()
+    assert create(batch(), no_counts) == 1
+    assert plan.value is None
+    lib.hepacc_plan_destroy(None)
