@@ -262,7 +262,7 @@ typedef struct {
     float lep_pt_min, lep_abseta_max, lep_iso_max;
     float jet_pt_min, jet_abseta_max, dr2_cut, btag_min;
     int32_t n_var;                         /* 1 .. HEPACC_MAX_VARIATIONS */
-    const float *scales;                   /* [n_var] jet-pt scale factors */
+    const float *scales;                   /* [n_var] jet-pt scale factors, finite and > 0 */
     int32_t nbins[HEPACC_CHAIN_NVARS];
     const float *edges;                    /* sum (nbins[h]+1) <= HEPACC_CHAIN_MAX_EDGES */
 } hepacc_chain_config;

@@ -32,7 +32,13 @@ hepacc_status make_params(const hepacc_chain_config* cfg, ChainParams& P) {
     P.dr2_cut = cfg->dr2_cut;
     P.btag_min = cfg->btag_min;
     P.n_var = cfg->n_var;
-    for (int k = 0; k < cfg->n_var; ++k) P.scales[k] = cfg->scales[k];
+    for (int k = 0; k < cfg->n_var; ++k) {
+        // the kernel decides the jet counts through thresholds, exact for
+        // positive finite scales only
+        if (!(cfg->scales[k] > 0.0f) || !std::isfinite(cfg->scales[k]))
+            return fail(HEPACC_ERR_INVALID_ARG, "scale %d is not a positive finite number", k);
+        P.scales[k] = cfg->scales[k];
+    }
     int ne = 0, nbt = 0;
     for (int h = 0; h < kNV; ++h) {
         const int nb = cfg->nbins[h];
@@ -46,6 +52,8 @@ hepacc_status make_params(const hepacc_chain_config* cfg, ChainParams& P) {
             if (i > 0 && !(cfg->edges[ne + i] >= cfg->edges[ne + i - 1]))
                 return fail(HEPACC_ERR_INVALID_ARG, "edges of histogram %d are not increasing", h);
         }
+        const float span = cfg->edges[ne + nb] - cfg->edges[ne];
+        P.invw[h] = span > 0.0f ? static_cast<float>(nb) / span : 0.0f;
         ne += nb + 1;
         nbt += nb + 2;
     }
@@ -107,8 +115,9 @@ void make_sample(const hepacc_event_batch* b, const hepacc_chain_outputs* out, S
 
 // Shared-memory layout for blocks of E threads (tiles of E events): stage
 // capacities from the mean objects per event (tiles that do not fit are read
-// from global memory), two stages, a 32-slot queue and jet acceptance flags
-// per warp, and the histograms of the placement (all of them in H_SMEM, a
+// from global memory), two stages, a 32-slot record queue, jet acceptance
+// flags, a 64-entry pair list and the event summaries per warp, and the
+// histograms of the placement (all of them in H_SMEM, a
 // 1/cluster slice in H_CLUSTER, none in H_GLOBAL). Returns whether it fits.
 bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_t kes, size_t bes,
                 const ChainParams& P, Layout& L) {
@@ -144,21 +153,27 @@ bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_
     add(E_ISO, 4, 2, cl);
     add(E_TIGHT, 1, 2, cl);
     auto up = [](size_t x) { return static_cast<uint32_t>((x + 127) & ~size_t(127)); };
+    // every region starts on a 16-byte boundary (8-byte fields live in
+    // several of them)
+    auto region = [](size_t& at, size_t bytes) {
+        at = (at + 15) & ~size_t(15);
+        const uint32_t start = static_cast<uint32_t>(at);
+        at += bytes;
+        return start;
+    };
     L.stage_bytes = up(kHdr + off);
-    size_t at = 2 * static_cast<size_t>(L.stage_bytes);
-    L.bars = static_cast<uint32_t>(at);
-    at += 32 + 48 + 16;   // four mbarriers, spans of the next tile
-    L.edges = static_cast<uint32_t>(at);
-    at += static_cast<size_t>((P.n_edges + 3) & ~3) * 4;
-    L.queue = static_cast<uint32_t>(at);
-    at += static_cast<size_t>(E) * R_WORDS * 4;
+    size_t at = 0;
+    region(at, 2 * static_cast<size_t>(L.stage_bytes));
+    L.bars = region(at, 32 + 48 + 16);   // four mbarriers, spans of the next tile
+    L.edges = region(at, static_cast<size_t>((P.n_edges + 3) & ~3) * 4);
+    L.queue = region(at, static_cast<size_t>(E) * R_WORDS * 4);
     L.acc_words = static_cast<int>(cj / 32 + 2);
-    L.acc = static_cast<uint32_t>(at);
-    at += static_cast<size_t>(E / 32) * L.acc_words * 4;
-    L.tri = static_cast<uint32_t>(at);
-    at += 256;
-    at = (at + 15) & ~size_t(15);
-    L.hist = static_cast<uint32_t>(at);
+    L.acc = region(at, static_cast<size_t>(E / 32) * L.acc_words * 4);
+    L.pairs = region(at, static_cast<size_t>(E / 32) * 64 * 2);
+    L.evs = region(at, static_cast<size_t>(E / 32) * kEvWords * 32 * 4);
+    L.sample = region(at, sizeof(SampleDesc));
+    L.tri = region(at, 256);
+    L.hist = region(at, 0);
     const size_t nbins = static_cast<size_t>(P.n_var) * P.total_bins;
     if (hmode == H_SMEM) at += nbins * (8 + 8 + 4);
     if (hmode == H_CLUSTER) {
@@ -417,7 +432,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
                              {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16},
                              {H_GLOBAL, 1, HEPACC_PLAN_HIST_GLOBAL}};
     for (const auto& m : modes)
-        for (int e = kMaxThreads; e >= 128 && (allowed & m[2]); e -= 32) {
+        for (int e = kMaxThreadsBatched; e >= 128 && (allowed & m[2]); e -= 32) {
             Candidate c;
             if (layout_for(e, m[0], m[1], lam_j, lam_l, kes, bes, p->P, c.L)) {
                 c.hmode = m[0];

@@ -12,12 +12,13 @@
 //    run independently (up to one tile apart) without block barriers; the
 //    tile spans are read two tiles ahead;
 //  * selection (thread = event, staged data): lepton selection, jet
-//    acceptance (|eta|, Delta R to the selected leptons), per jet-pt
-//    variation the jet counts that decide the event; for a passing event
-//    the same thread then gathers HT, the mass sum, the leading jets and the
-//    max-|sum pT| triplet (ranked in registers) from shared memory and
-//    queues the (event, variation) with the jets' four-momenta in a per-warp
-//    queue;
+//    acceptance (|eta|, Delta R to the selected leptons, lanes over jets),
+//    and per event the two pt thresholds that decide every jet-pt variation
+//    (second-largest accepted jet pt, largest accepted b-tagged jet pt);
+//  * pairs (thread = passing (event, variation), 32 at a time per warp):
+//    the pair's lane gathers the jet counts, HT, the mass sum, the leading
+//    jets and the max-|sum pT| triplet from shared memory and writes a
+//    self-contained record (with the jets' four-momenta) to a per-warp queue;
 //  * masses (thread = queued pair, 32 at a time per warp): pair and triplet
 //    invariant masses and the 20 variables, pure arithmetic;
 //  * fill: lane h bins variable h of every queued entry (no two lanes of a
@@ -45,8 +46,15 @@ constexpr int NC = 15;            // staged columns
 constexpr int kNV = HEPACC_CHAIN_NVARS;
 constexpr int kQ = kNV + 1;       // fill entry: 20 variables + variation
 constexpr int kScratch = 10;      // selected jets ranked from a queue slot (2 x 10 words of it)
+// Largest block of each launch form. Register allocation rounds a block of
+// 320 threads up like one of 384, which caps a thread at 168 registers; 256
+// threads allow 255. Single-sample launches run more warps per SM at 168
+// (some spilling); batched launches, whose loop over samples and pair work
+// keep more live state, run spill-free at 256.
 constexpr int kMaxThreads = 320;
+constexpr int kMaxThreadsBatched = 256;
 constexpr int kHdr = 96;          // stage header: spans, staged flag, column offsets
+constexpr int kEvWords = 12;      // event summary handed to the pairs
 
 enum : int { J_PT = 0, J_ETA, J_PHI, J_MASS, J_BTAG, M_PT, M_ETA, M_PHI, M_ISO, M_TIGHT, E_PT, E_ETA, E_PHI, E_ISO, E_TIGHT };
 
@@ -60,6 +68,7 @@ struct ChainParams {
     int nbins[kNV];
     int eoff[kNV];      // first edge of histogram h
     int boff[kNV];      // first bin of histogram h inside a variation block
+    float invw[kNV];    // bins per unit of histogram h (first guess of the bin search)
     float edges[HEPACC_CHAIN_MAX_EDGES];
 };
 
@@ -123,6 +132,9 @@ struct Layout {
     uint32_t edges;        // n_edges floats
     uint32_t queue;        // per warp 32 slots of R_WORDS words
     uint32_t acc;          // per warp acc_words words of jet acceptance flags
+    uint32_t pairs;        // per warp 64 queued (event lane, variation) pairs, uint16
+    uint32_t evs;          // per warp kEvWords x 32 words: the events' summaries
+    uint32_t sample;       // batched launches: the current sample's descriptor
     int acc_words;
     uint32_t tri;          // triplet table (uint16 per triplet, colex order)
     uint32_t hist;         // histograms (H_SMEM: all bins, H_CLUSTER: this block's slice)
@@ -131,11 +143,13 @@ struct Layout {
 };
 
 // A queued (event, variation): words of a per-warp queue slot. Jets are
-// (pt_k, eta, phi, mass); the leading one also carries btag.
+// (pt_k, eta, phi, mass); the leading one also carries btag. The slot
+// stride is odd so that lanes reading one word of their slots hit distinct
+// shared-memory banks.
 enum : int {
     R_E = 0, R_K, R_NJ, R_IDX, R_TAB, R_TC, R_HT, R_SUMM, R_MAXBT, R_BEST, R_W,
     R_LPT, R_LETA, R_LPHI, R_LISO,
-    R_J1 = 15, R_J2 = 20, R_T1 = 24, R_T2 = 28, R_T3 = 32, R_WORDS = 36
+    R_J1 = 15, R_J2 = 20, R_T1 = 24, R_T2 = 28, R_T3 = 32, R_WORDS = 37
 };
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
@@ -171,7 +185,7 @@ __device__ __forceinline__ void put4(uint32_t* q, float a, float b, float c, flo
 }
 
 template <typename KT, typename BT, typename OffT, bool DEBUG, int HMODE, bool MULTI>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant__ Layout L,
+__global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k_chain(const __grid_constant__ Layout L,
                                                           const __grid_constant__ ChainParams P,
                                                           const __grid_constant__ BatchDesc B) {
     unsigned char* smem = g_dyn_smem;
@@ -219,14 +233,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
     __syncthreads();
     if (HMODE == H_CLUSTER) cluster_sync_all();
 
-    // the sample being processed (set at the top of the sample loop; always
-    // 0 for single-sample launches)
-    int si = 0;
-    const OffT* offs[3] = {nullptr, nullptr, nullptr};
+    // The sample being processed: single-sample launches read its
+    // descriptor from the kernel parameters; batched ones copy the current
+    // sample's descriptor to shared memory at the top of the sample loop
+    // (its fields are then read where they are used instead of occupying
+    // registers for the whole sample).
+    SampleDesc* cur = reinterpret_cast<SampleDesc*>(smem + L.sample);
+    auto SD = [&]() -> const SampleDesc& {
+        if constexpr (MULTI)
+            return *cur;
+        else
+            return B.s[0];
+    };
+    auto offs = [&](int c) { return static_cast<const OffT*>(SD().off[c]); };
     int64_t n = 0;
     int64_t ntiles = 0;
     const int64_t grid = gridDim.x;
-    const float* weight = nullptr;
 
     // thread 0: first and last element of every collection in tile tt
     auto load_span = [&](int64_t tt, int64_t (&S)[3], int64_t (&T)[3]) {
@@ -234,8 +256,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         const int64_t z = a + E < n ? a + E : n;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            S[c] = ldoff(offs[c], a);
-            T[c] = ldoff(offs[c], z);
+            S[c] = ldoff(offs(c), a);
+            T[c] = ldoff(offs(c), z);
         }
     };
     // thread 0: header of stage b and the bulk copies of the tile's spans
@@ -248,7 +270,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const ColSpec& cs = L.col[c];
-            const uintptr_t cb = reinterpret_cast<uintptr_t>(B.s[si].col[c]);
+            const uintptr_t cb = reinterpret_cast<uintptr_t>(SD().col[c]);
             const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
             const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
             const uintptr_t bytes = T[cs.coll] > S[cs.coll] ? ((z + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)) : 0;
@@ -267,7 +289,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             for (int c = 0; c < NC; ++c) {
                 const ColSpec& cs = L.col[c];
                 if (T[cs.coll] <= S[cs.coll]) continue;
-                const uintptr_t cb = reinterpret_cast<uintptr_t>(B.s[si].col[c]);
+                const uintptr_t cb = reinterpret_cast<uintptr_t>(SD().col[c]);
                 const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
                 const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
                 const uintptr_t a16 = a & ~uintptr_t(15);
@@ -281,7 +303,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
 
     // Masses and fill for this warp's queued records [0, m) (warp-uniform).
     auto flush = [&](int m) {
-        const ChainOut& out = B.s[si].out;
+        const ChainOut& out = SD().out;
         const uint32_t* r = my_q + lane * R_WORDS;   // this lane's record
         const bool have = lane < m;
         float var[kNV];
@@ -367,14 +389,36 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             q[kNV] = pass ? static_cast<uint32_t>(k) : 0xffffffffu;
         }
         __syncwarp();
-        // lane h fills histogram h for every queued entry (distinct lanes,
-        // distinct histograms: no two lanes of the warp touch the same bin)
+        if (HMODE == H_GLOBAL) {
+            // global histograms: lane j fills every histogram of entry j
+            // (lanes that meet on a bin are serialised by the L2 atomics)
+            if (lane < m) {
+                const uint32_t* q = my_q + lane * R_WORDS;
+                const uint32_t kk = q[kNV];
+                const double wd = static_cast<double>(__uint_as_float(q[19]));
+                if (kk != 0xffffffffu) {
+                    for (int h = 0; h < kNV; ++h) {
+                        const float* eh = s_edges + P.eoff[h];
+                        const int nb_h = P.nbins[h];
+                        const int bin = find_bin(__uint_as_float(q[h]), eh, nb_h, P.invw[h]);
+                        if (bin < 0) continue;
+                        const int at = static_cast<int>(kk) * P.total_bins + P.boff[h] + bin;
+                        atomicAdd(&out.counts[at], 1ull);
+                        atomicAdd(&out.sumw[at], wd);
+                        if (out.sumw2) atomicAdd(&out.sumw2[at], wd * wd);
+                    }
+                }
+            }
+            __syncwarp();
+            return;
+        }
+        // shared-memory histograms: lane h fills histogram h for every
+        // queued entry (no two lanes of the warp touch the same bin)
         if (lane < kNV) {
             const int h = lane;
             const float* eh = s_edges + P.eoff[h];
             const int nb_h = P.nbins[h];
-            const float span = eh[nb_h] - eh[0];
-            const float invw = span > 0.0f ? static_cast<float>(nb_h) / span : 0.0f;
+            const float invw = P.invw[h];
             const int boff = P.boff[h];
             for (int j = 0; j < m; ++j) {
                 const uint32_t* q = my_q + j * R_WORDS;
@@ -388,16 +432,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                     atomicAdd(&s_c[at], 1u);
                     atomicAdd(&s_w[at], wd);
                     if (out.sumw2) atomicAdd(&s_w2[at], wd * wd);
-                } else if (HMODE == H_CLUSTER) {
+                } else {
                     const uint32_t rk = static_cast<uint32_t>(at) / static_cast<uint32_t>(L.hist_slice);
                     const int loc = at - static_cast<int>(rk) * L.hist_slice;
                     red_cluster_u32(map_to_rank(smem_addr(s_c + loc), rk), 1u);
                     red_cluster_f64(map_to_rank(smem_addr(s_w + loc), rk), wd);
                     if (out.sumw2) red_cluster_f64(map_to_rank(smem_addr(s_w2 + loc), rk), wd * wd);
-                } else {
-                    atomicAdd(&out.counts[at], 1ull);
-                    atomicAdd(&out.sumw[at], wd);
-                    if (out.sumw2) atomicAdd(&out.sumw2[at], wd * wd);
                 }
             }
         }
@@ -412,13 +452,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
     int b = 0;
     bool stop = false;   // a bounded wait gave up: skip the remaining work, keep the barriers
     for (int sl = 0; sl < (MULTI ? B.n_samples : 1); ++sl) {
-    si = MULTI ? sl : 0;
-    offs[0] = static_cast<const OffT*>(B.s[si].off[0]);
-    offs[1] = static_cast<const OffT*>(B.s[si].off[1]);
-    offs[2] = static_cast<const OffT*>(B.s[si].off[2]);
-    n = B.s[si].n;
+    if constexpr (MULTI) {
+        __syncthreads();   // every warp is done with the previous descriptor
+        for (int i = tid; i < static_cast<int>(sizeof(SampleDesc) / 8); i += E)
+            reinterpret_cast<uint64_t*>(cur)[i] = reinterpret_cast<const uint64_t*>(&B.s[sl])[i];
+        __syncthreads();
+    }
+    n = SD().n;
     ntiles = (n + E - 1) / E;
-    weight = B.s[si].weight;
     int64_t tile = stop ? ntiles : blockIdx.x;
     int64_t cs_[3] = {0, 0, 0}, ct_[3] = {0, 0, 0};
     if (tile < ntiles) {
@@ -438,8 +479,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         const int64_t elo = e < n ? e : n, ehi = e + 1 < n ? e + 1 : n;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            cs_[c] = ldoff(offs[c], elo);
-            ct_[c] = ldoff(offs[c], ehi);
+            cs_[c] = ldoff(offs(c), elo);
+            ct_[c] = ldoff(offs(c), ehi);
         }
     }
     for (; tile < ntiles; tile += grid) {
@@ -461,8 +502,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             const int64_t elo = e < n ? e : n, ehi = e + 1 < n ? e + 1 : n;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                ns_[c] = ldoff(offs[c], elo);
-                nt_[c] = ldoff(offs[c], ehi);
+                ns_[c] = ldoff(offs(c), elo);
+                nt_[c] = ldoff(offs(c), ehi);
             }
         }
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(full[b], fpar[b]))) {   // error word set; this warp stops
@@ -486,7 +527,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         StagedCols sc;
         DirectCols dc;
         dc.L = &L;
-        dc.base = B.s[si].col;
+        dc.base = SD().col;
 #pragma unroll
         for (int c = 0; c < 3; ++c) dc.S[c] = hdr[c];
         if (staged) {
@@ -561,7 +602,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             else
                 lep_vals(dc);
         }
-        if (DEBUG && valid && B.s[si].out.ev_nlep) B.s[si].out.ev_nlep[e] = nlep;
+        if (DEBUG && valid && SD().out.ev_nlep) SD().out.ev_nlep[e] = nlep;
         // without per-event outputs only single-lepton events can pass
         const bool active = valid && (DEBUG || nlep == 1);
         const unsigned amask = __ballot_sync(0xffffffffu, active);
@@ -569,7 +610,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
         // jet acceptance (|eta|, Delta R >= cut to every selected lepton of
         // the jet's event), lanes over jets; one word of flags per 32 jets
         const int nround = (W1[0] - W0[0] + 31) >> 5;
-        const bool acc_cached = nround <= L.acc_words;
         uint32_t* accw = reinterpret_cast<uint32_t*>(smem + L.acc) + warp * L.acc_words;
         // Delta R test of jet (eta, phi) against every selected lepton of the
         // event whose lepton ranges are given (events with several leptons)
@@ -624,52 +664,61 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                 accept(dc);
         }
         __syncwarp();
-        // acceptance of jet i by its own lane (flags, or recomputed past them)
-        auto acc_of = [&](const auto& T, int i) -> bool {
+        // An event as the jet selection sees it: its jets, leptons and the
+        // selected-lepton summary (taken from the event's own lane).
+        struct Ev {
+            int j0, j1, m0, m1, e0, e1, nlep;
+            float leta, lphi;
+        };
+        // acceptance of jet i of event ev (flags, or recomputed past them)
+        auto acc_of = [&](const auto& T, const Ev& ev, int i) -> bool {
             const int q = i - W0[0];
             if ((q >> 5) < L.acc_words) return ((accw[q >> 5] >> (q & 31)) & 1u) != 0;
             const float eta = Elem<KT>::f(T.template ld<KT>(J_ETA, i));
             if (!(fabsf(eta) < P.jet_abseta_max)) return false;
             const float phi = Elem<KT>::f(T.template ld<KT>(J_PHI, i));
-            if (nlep == 1) return !(dr2_f32(eta, phi, leta, lphi) < P.dr2_cut);
-            if (nlep == 0) return true;
-            return far_from_all(T, eta, phi, rs[1], rt[1], rs[2], rt[2]);
+            if (ev.nlep == 1) return !(dr2_f32(eta, phi, ev.leta, ev.lphi) < P.dr2_cut);
+            if (ev.nlep == 0) return true;
+            return far_from_all(T, eta, phi, ev.m0, ev.m1, ev.e0, ev.e1);
         };
-        auto jet_sel = [&](const auto& T, int i, float s, float& ptk) -> bool {
-            if (!acc_of(T, i)) return false;
+        auto jet_sel = [&](const auto& T, const Ev& ev, int i, float s, float& ptk) -> bool {
+            if (!acc_of(T, ev, i)) return false;
             ptk = __fmul_rn(Elem<KT>::f(T.template ld<KT>(J_PT, i)), s);
             return ptk > P.jet_pt_min;
         };
-        // per variation: jet and b-jet counts, lanes over jets
-        auto count = [&](const auto& T, float s, int& njet, int& nbj) {
-            for (int base = W0[0]; base < W1[0]; base += 32) {
-                const int p = base + lane;
-                bool sel = false, bsel = false;
-                if (p < W1[0] && acc_cached && ((accw[(base - W0[0]) >> 5] >> lane) & 1u)) {
-                    sel = __fmul_rn(Elem<KT>::f(T.template ld<KT>(J_PT, p)), s) > P.jet_pt_min;
-                    bsel = sel && Elem<BT>::f(T.template ld<BT>(J_BTAG, p)) > P.btag_min;
+        const Ev own = {rs[0], rt[0], rs[1], rt[1], rs[2], rt[2], nlep, leta, lphi};
+        // The jet counts decide the event through two thresholds: x -> fl(x * s)
+        // is non-decreasing for s > 0, so at least two selected jets (pt_k >
+        // cut) exist iff the second-largest accepted pt p2 has fl(p2 * s) >
+        // cut, and a selected b-jet exists iff the largest accepted b-tagged
+        // pt pb has fl(pb * s) > cut. p2 and pb do not depend on the
+        // variation: one pass over the event's jets, by its own lane.
+        float p1 = -INFINITY, p2 = -INFINITY, pb = -INFINITY;
+        auto thresholds = [&](const auto& T) {
+            for (int i = rs[0]; i < rt[0]; ++i) {
+                if (!acc_of(T, own, i)) continue;
+                const float pt = Elem<KT>::f(T.template ld<KT>(J_PT, i));
+                if (pt > p1) {
+                    p2 = p1;
+                    p1 = pt;
+                } else if (pt > p2) {
+                    p2 = pt;
                 }
-                const unsigned rm = range_mask(rs[0], rt[0], base);
-                njet += __popc(__ballot_sync(0xffffffffu, sel) & rm);
-                nbj += __popc(__ballot_sync(0xffffffffu, bsel) & rm);
-            }
-            if (!acc_cached && active) {
-                // flags not cached for this tile: count this lane's jets itself
-                njet = 0;
-                nbj = 0;
-                for (int i = rs[0]; i < rt[0]; ++i) {
-                    float ptk;
-                    if (!jet_sel(T, i, s, ptk)) continue;
-                    ++njet;
-                    nbj += Elem<BT>::f(T.template ld<BT>(J_BTAG, i)) > P.btag_min ? 1 : 0;
-                }
+                if (pt > pb && Elem<BT>::f(T.template ld<BT>(J_BTAG, i)) > P.btag_min) pb = pt;
             }
         };
-        // a queued event, by its own lane: HT and the mass sum (element
-        // order), leading pair, max btag; the transverse momenta and tile
-        // indices of the first kScratch selected jets go to the slot (its
-        // jet area and first words are free until the record is written)
-        auto sums = [&](const auto& T, float s, uint32_t* r, int& nsel, int& lead, int& sub) {
+        if (active) {
+            if (staged)
+                thresholds(sc);
+            else
+                thresholds(dc);
+        }
+        // a queued (event, variation): jet and b-jet counts, HT and the mass
+        // sum (element order), leading pair, max btag; the transverse momenta
+        // and tile indices of the first kScratch selected jets go to the slot
+        // (its jet area and first words are free until the record is written)
+        auto sums = [&](const auto& T, const Ev& ev, float s, uint32_t* r, int& nsel, int& nbj, int& lead,
+                        int& sub) {
             float ht = 0.0f, summ = 0.0f, maxbt = qnan(), lead_pt = 0.0f, sub_pt = 0.0f;
             lead = -1;
             sub = -1;
@@ -677,10 +726,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             float* sy = sx + kScratch;
             int16_t* li = reinterpret_cast<int16_t*>(r);
             nsel = 0;
-            for (int i = rs[0]; i < rt[0]; ++i) {
+            nbj = 0;
+            for (int i = ev.j0; i < ev.j1; ++i) {
                 float ptk;
-                if (!jet_sel(T, i, s, ptk)) continue;
+                if (!jet_sel(T, ev, i, s, ptk)) continue;
                 const float bt = Elem<BT>::f(T.template ld<BT>(J_BTAG, i));
+                nbj += bt > P.btag_min ? 1 : 0;
                 ht = __fadd_rn(ht, ptk);
                 summ = __fadd_rn(summ, Elem<KT>::f(T.template ld<KT>(J_MASS, i)));
                 if (lead < 0 || ptk > lead_pt) {
@@ -706,23 +757,43 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
             r[R_SUMM] = __float_as_uint(summ);
             r[R_MAXBT] = __float_as_uint(maxbt);
         };
-        // more selected jets than the scratch holds: the owning lane ranks all
-        // triplets itself from the tile
-        auto slow_triplet = [&](const auto& T, float s, float& best, int& ta, int& tb, int& tc) {
-            for (int a = rs[0]; a < rt[0]; ++a) {
+        // max |sum pT| triplet among the first n <= kScratch selected jets of
+        // a slot: all C(n,3) triplets (colex table), largest value wins, ties
+        // go to the smallest (a, b, c), i.e. the first in lexicographic order
+        auto triplet = [&](const uint32_t* r, int n, float& best, int& key) {
+            const float* qx = reinterpret_cast<const float*>(r + R_J1);
+            const float* qy = qx + kScratch;
+            const int ntri = n * (n - 1) * (n - 2) / 6;
+            best = -1.0f;
+            key = 0xfff;
+            for (int t = 0; t < ntri; ++t) {
+                const int abc = s_tri[t];
+                const int a = abc & 15, b2 = (abc >> 4) & 15, c = abc >> 8;
+                const float tx = (qx[a] + qx[b2]) + qx[c], ty = (qy[a] + qy[b2]) + qy[c];
+                const float val = tx * tx + ty * ty;
+                const int kk = (a << 8) | (b2 << 4) | c;
+                if (val > best || (val == best && kk < key)) {
+                    best = val;
+                    key = kk;
+                }
+            }
+        };
+        // more selected jets than the scratch holds: all triplets from the tile
+        auto slow_triplet = [&](const auto& T, const Ev& ev, float s, float& best, int& ta, int& tb, int& tc) {
+            for (int a = ev.j0; a < ev.j1; ++a) {
                 float pa;
-                if (!jet_sel(T, a, s, pa)) continue;
+                if (!jet_sel(T, ev, a, s, pa)) continue;
                 float sa, ca;
                 __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, a)), &sa, &ca);
-                for (int bq = a + 1; bq < rt[0]; ++bq) {
-                    float pb;
-                    if (!jet_sel(T, bq, s, pb)) continue;
+                for (int bq = a + 1; bq < ev.j1; ++bq) {
+                    float pb2;
+                    if (!jet_sel(T, ev, bq, s, pb2)) continue;
                     float sb, cb;
                     __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, bq)), &sb, &cb);
-                    const float bx = pa * ca + pb * cb, by = pa * sa + pb * sb;
-                    for (int c = bq + 1; c < rt[0]; ++c) {
+                    const float bx = pa * ca + pb2 * cb, by = pa * sa + pb2 * sb;
+                    for (int c = bq + 1; c < ev.j1; ++c) {
                         float pc;
-                        if (!jet_sel(T, c, s, pc)) continue;
+                        if (!jet_sel(T, ev, c, s, pc)) continue;
                         float sc2, cc;
                         __sincosf(Elem<KT>::f(T.template ld<KT>(J_PHI, c)), &sc2, &cc);
                         const float tx = bx + pc * cc, ty = by + pc * sc2;
@@ -742,100 +813,80 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                  Elem<KT>::f(T.template ld<KT>(J_PHI, i)), Elem<KT>::f(T.template ld<KT>(J_MASS, i)));
         };
 
-        const float w = valid ? weight[e] : 0.0f;
-        for (int k = 0; k < P.n_var; ++k) {
-            const float s = P.scales[k];
-            int njet = 0, nbj = 0;
-            if (amask) {
-                if (staged)
-                    count(sc, s, njet, nbj);
-                else
-                    count(dc, s, njet, nbj);
-            }
-            if (!active) {
-                njet = 0;
-                nbj = 0;
-            }
-            const bool pass = active && nlep == 1 && njet >= 2 && nbj >= 1;
-            const bool enq = DEBUG ? valid : pass;
-            const unsigned emask = __ballot_sync(0xffffffffu, enq);
-            const int m = __popc(emask);
-            if (m == 0) continue;
+        // The (event, variation) pairs to queue, 32 at a time with one lane
+        // per pair: the event's lane hands over its summary, the pair's lane
+        // builds the record (jet sums, triplet, four-momenta) from the stage.
+        // each event's summary goes to shared memory (field-major, lane
+        // minor), where the pairs read it
+        uint16_t* my_pairs = reinterpret_cast<uint16_t*>(smem + L.pairs) + warp * 64;
+        uint32_t* my_evs = reinterpret_cast<uint32_t*>(smem + L.evs) + warp * (kEvWords * 32);
+        my_evs[0 * 32 + lane] = static_cast<uint32_t>(rs[0]);
+        my_evs[1 * 32 + lane] = static_cast<uint32_t>(rt[0]);
+        my_evs[2 * 32 + lane] = static_cast<uint32_t>(rs[1]);
+        my_evs[3 * 32 + lane] = static_cast<uint32_t>(rt[1]);
+        my_evs[4 * 32 + lane] = static_cast<uint32_t>(rs[2]);
+        my_evs[5 * 32 + lane] = static_cast<uint32_t>(rt[2]);
+        my_evs[6 * 32 + lane] = static_cast<uint32_t>(nlep);
+        my_evs[7 * 32 + lane] = __float_as_uint(leta);
+        my_evs[8 * 32 + lane] = __float_as_uint(lphi);
+        my_evs[9 * 32 + lane] = __float_as_uint(valid ? SD().weight[e] : 0.0f);
+        my_evs[10 * 32 + lane] = __float_as_uint(lpt);
+        my_evs[11 * 32 + lane] = __float_as_uint(liso);
+        __syncwarp();
+        auto process = [&](int m) {
             if (qcount + m > 32) {
                 flush(qcount);
                 qcount = 0;
             }
-            uint32_t* r = my_q + (qcount + __popc(emask & lt_mask)) * R_WORDS;
-            int nsel = 0, lead = -1, sub = -1;
-            if (enq) {
+            const bool mine = lane < m;
+            const int pk = my_pairs[mine ? lane : 0];
+            const int el = pk & 31;
+            Ev ev;
+            ev.j0 = static_cast<int>(my_evs[0 * 32 + el]);
+            ev.j1 = static_cast<int>(my_evs[1 * 32 + el]);
+            ev.m0 = static_cast<int>(my_evs[2 * 32 + el]);
+            ev.m1 = static_cast<int>(my_evs[3 * 32 + el]);
+            ev.e0 = static_cast<int>(my_evs[4 * 32 + el]);
+            ev.e1 = static_cast<int>(my_evs[5 * 32 + el]);
+            ev.nlep = static_cast<int>(my_evs[6 * 32 + el]);
+            ev.leta = __uint_as_float(my_evs[7 * 32 + el]);
+            ev.lphi = __uint_as_float(my_evs[8 * 32 + el]);
+            uint32_t* r = my_q + (qcount + (mine ? lane : 0)) * R_WORDS;
+            const int k = (pk >> 5) & 63;
+            const bool pass = (pk & 0x800) != 0;
+            const float s = P.scales[k];
+            int nsel = 0, nbj = 0, lead = -1, sub = -1;
+            if (mine) {
                 if (staged)
-                    sums(sc, s, r, nsel, lead, sub);
+                    sums(sc, ev, s, r, nsel, nbj, lead, sub);
                 else
-                    sums(dc, s, r, nsel, lead, sub);
+                    sums(dc, ev, s, r, nsel, nbj, lead, sub);
             }
             __syncwarp();
-            // max |sum pT| triplet of every queued event: lanes over its
-            // triplets (colex order table), largest value wins, ties go to the
-            // smallest (a, b, c), i.e. the first in lexicographic order
-            float my_best = -1.0f;
-            int my_key = -1;
-            for (unsigned em = emask; em; em &= em - 1) {
-                const int L = __ffs(em) - 1;
-                const int nL = __shfl_sync(0xffffffffu, nsel, L);
-                if (nL < 3 || nL > kScratch) continue;
-                const float* qx = reinterpret_cast<const float*>(my_q + (qcount + __popc(emask & ((1u << L) - 1u))) * R_WORDS + R_J1);
-                const float* qy = qx + kScratch;
-                const int ntri = nL * (nL - 1) * (nL - 2) / 6;
-                float bv = -1.0f;
-                int bk = 0xfff;
-                for (int t = lane; t < ntri; t += 32) {
-                    const int abc = s_tri[t];
-                    const int a = abc & 15, b2 = (abc >> 4) & 15, c = abc >> 8;
-                    const float tx = (qx[a] + qx[b2]) + qx[c], ty = (qy[a] + qy[b2]) + qy[c];
-                    const float val = tx * tx + ty * ty;
-                    const int key = (a << 8) | (b2 << 4) | c;
-                    if (val > bv || (val == bv && key < bk)) {
-                        bv = val;
-                        bk = key;
-                    }
-                }
-#pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, bv, d);
-                    const int ok = __shfl_xor_sync(0xffffffffu, bk, d);
-                    if (ov > bv || (ov == bv && ok < bk)) {
-                        bv = ov;
-                        bk = ok;
-                    }
-                }
-                if (lane == L) {
-                    my_best = bv;
-                    my_key = bk;
-                }
-            }
-            if (enq) {
-                float best = -1.0f;
+            float best = -1.0f;
+            int key = 0xfff;
+            if (mine && nsel >= 3 && nsel <= kScratch) triplet(r, nsel, best, key);
+            if (mine) {
                 int ta = -1, tb = -1, tc = -1;
-                const int16_t* li = reinterpret_cast<const int16_t*>(r);
                 if (nsel >= 3 && nsel <= kScratch) {
-                    best = my_best;
-                    ta = li[my_key >> 8];
-                    tb = li[(my_key >> 4) & 15];
-                    tc = li[my_key & 15];
+                    const int16_t* li = reinterpret_cast<const int16_t*>(r);
+                    ta = li[key >> 8];
+                    tb = li[(key >> 4) & 15];
+                    tc = li[key & 15];
                 } else if (nsel > kScratch) {
                     if (staged)
-                        slow_triplet(sc, s, best, ta, tb, tc);
+                        slow_triplet(sc, ev, s, best, ta, tb, tc);
                     else
-                        slow_triplet(dc, s, best, ta, tb, tc);
+                        slow_triplet(dc, ev, s, best, ta, tb, tc);
                 }
                 r[R_BEST] = __float_as_uint(best);
-                const int l16 = lead < 0 ? 0xffff : (lead - rs[0]) & 0xffff;
-                const int s16 = sub < 0 ? 0xffff : (sub - rs[0]) & 0xffff;
+                const int l16 = lead < 0 ? 0xffff : (lead - ev.j0) & 0xffff;
+                const int s16 = sub < 0 ? 0xffff : (sub - ev.j0) & 0xffff;
                 r[R_IDX] = static_cast<uint32_t>(l16) | (static_cast<uint32_t>(s16) << 16);
-                const int a16 = ta < 0 ? 0xffff : (ta - rs[0]) & 0xffff;
-                const int b16 = tb < 0 ? 0xffff : (tb - rs[0]) & 0xffff;
+                const int a16 = ta < 0 ? 0xffff : (ta - ev.j0) & 0xffff;
+                const int b16 = tb < 0 ? 0xffff : (tb - ev.j0) & 0xffff;
                 r[R_TAB] = static_cast<uint32_t>(a16) | (static_cast<uint32_t>(b16) << 16);
-                r[R_TC] = static_cast<uint32_t>(tc < 0 ? -1 : tc - rs[0]);
+                r[R_TC] = static_cast<uint32_t>(tc < 0 ? -1 : tc - ev.j0);
                 auto write4 = [&](const auto& T) {
                     if (lead >= 0) {
                         jet4(T, s, lead, r + R_J1);
@@ -852,18 +903,42 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
                     write4(sc);
                 else
                     write4(dc);
-                r[R_E] = static_cast<uint32_t>(e);
-                r[R_K] = static_cast<uint32_t>(k) | (pass ? 0x100u : 0u) | (static_cast<uint32_t>(min(nlep, 0xffff)) << 16);
-                r[R_NJ] = static_cast<uint32_t>(min(njet, 0xffff)) | (static_cast<uint32_t>(min(nbj, 0xffff)) << 16);
-                r[R_W] = __float_as_uint(w);
-                r[R_LPT] = __float_as_uint(lpt);
-                r[R_LETA] = __float_as_uint(leta);
-                r[R_LPHI] = __float_as_uint(lphi);
-                r[R_LISO] = __float_as_uint(liso);
+                r[R_E] = static_cast<uint32_t>(tile * E + warp * 32 + el);
+                r[R_K] = static_cast<uint32_t>(k) | (pass ? 0x100u : 0u) |
+                         (static_cast<uint32_t>(min(ev.nlep, 0xffff)) << 16);
+                r[R_NJ] = static_cast<uint32_t>(min(nsel, 0xffff)) | (static_cast<uint32_t>(min(nbj, 0xffff)) << 16);
+                r[R_W] = my_evs[9 * 32 + el];
+                r[R_LPT] = my_evs[10 * 32 + el];
+                r[R_LETA] = __float_as_uint(ev.leta);
+                r[R_LPHI] = __float_as_uint(ev.lphi);
+                r[R_LISO] = my_evs[11 * 32 + el];
             }
             __syncwarp();
             qcount += m;
+        };
+        int npairs = 0;
+        for (int k = 0; k < P.n_var; ++k) {
+            const float s = P.scales[k];
+            const bool pass = active && nlep == 1 && __fmul_rn(p2, s) > P.jet_pt_min &&
+                              __fmul_rn(pb, s) > P.jet_pt_min;
+            const bool enq = DEBUG ? valid : pass;
+            const unsigned emask = __ballot_sync(0xffffffffu, enq);
+            if (emask == 0u) continue;
+            if (enq) my_pairs[npairs + __popc(emask & lt_mask)] = static_cast<uint16_t>(lane | (k << 5) | (pass ? 0x800 : 0));
+            npairs += __popc(emask);
+            __syncwarp();
+            if (npairs >= 32) {
+                process(32);
+                // the rest (fewer than 32) moves to the front
+                const int rest = npairs - 32;
+                const uint16_t v = lane < rest ? my_pairs[32 + lane] : 0;
+                __syncwarp();
+                if (lane < rest) my_pairs[lane] = v;
+                __syncwarp();
+                npairs = rest;
+            }
         }
+        if (npairs > 0) process(npairs);
         // this warp is done with the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(empty[b]);
@@ -880,7 +955,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_chain(const __grid_constant_
     // the sample's histograms: block-private or cluster-slice copies go to
     // the sample's outputs and are cleared for the next sample
     if (HMODE != H_GLOBAL) {
-        const ChainOut& out = B.s[si].out;
+        const ChainOut& out = SD().out;
         if (HMODE == H_CLUSTER)
             cluster_sync_all();
         else

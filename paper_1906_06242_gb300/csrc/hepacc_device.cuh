@@ -171,12 +171,15 @@ __device__ __forceinline__ MassObj mass_obj(float pt, float eta, float phi, floa
     o.m = m;
     const float m2 = m * m;
     o.mt = sqrtf(pt * pt + m2);
-    const float ex = expf(eta);
-    const float emx = 1.0f / ex;
+    // e^eta to a few 1e-7 relative (the approximate exponential): it enters
+    // the energy and the small rapidity correction c only, never a
+    // difference that cancels
+    const float ex = __expf(eta);
+    const float emx = __frcp_rn(ex);
     const float p = pt * 0.5f * (ex + emx);   // pt cosh(eta)
     o.e = sqrtf(p * p + m2);
     if (pt > 0.0f) {
-        const float u = (m2 / (o.e + p)) / pt;
+        const float u = __fdividef(__fdividef(m2, o.e + p), pt);
         o.c = 0.5f * (log1pf(u * emx) - log1pf(u * ex));
     } else {
         o.c = 0.0f;
@@ -188,11 +191,13 @@ __device__ __forceinline__ MassObj mass_obj(float pt, float eta, float phi, floa
 __device__ __forceinline__ float pair_dot(const MassObj& a, const MassObj& b) {
     if (a.pt == 0.0f) return a.m * b.e;
     if (b.pt == 0.0f) return b.m * a.e;
-    const float a_ij = (a.pt * a.pt * b.m * b.m + a.m * a.m * b.pt * b.pt + a.m * a.m * b.m * b.m) /
-                       (a.mt * b.mt + a.pt * b.pt);
+    const float a_ij = __fdividef(a.pt * a.pt * b.m * b.m + a.m * a.m * b.pt * b.pt + a.m * a.m * b.m * b.m,
+                                  a.mt * b.mt + a.pt * b.pt);
     const float hy = 0.5f * ((a.eta - b.eta) + (a.c - b.c));
     const float sh = sinhf(hy);
-    const float sp = sinf(0.5f * (a.phi - b.phi));
+    // sin(dphi / 2) as sinpi(dphi / (2 pi)): exact argument reduction, so
+    // small angles keep their relative accuracy
+    const float sp = sinpif((a.phi - b.phi) * 0.159154943f);
     return a_ij + 2.0f * a.mt * b.mt * sh * sh + 2.0f * a.pt * b.pt * sp * sp;
 }
 
