@@ -44,8 +44,12 @@ DeviceInfo device_info() {
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&d.max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&d.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         if (d.sms <= 0) d.sms = 1;
         if (d.smem_optin <= 0) d.smem_optin = 48 * 1024;
+        if (d.smem_per_sm <= 0) d.smem_per_sm = d.smem_optin;
+        if (d.smem_reserved < 0) d.smem_reserved = 0;
         cache[dev] = d;
         have[dev] = true;
     }

@@ -120,7 +120,7 @@ void make_sample(const hepacc_event_batch* b, const hepacc_chain_outputs* out, S
 // histograms of the placement (all of them in H_SMEM, a
 // 1/cluster slice in H_CLUSTER, none in H_GLOBAL). Returns whether it fits.
 bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_t kes, size_t bes,
-                const ChainParams& P, Layout& L) {
+                int blocks_per_sm, const ChainParams& P, Layout& L) {
     std::memset(&L, 0, sizeof L);
     auto cap_of = [&](double lam) {
         const double m = E * lam;
@@ -181,7 +181,9 @@ bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_
         at += static_cast<size_t>(L.hist_slice) * (8 + 8 + 4);
     }
     L.total = static_cast<uint32_t>((at + 15) & ~size_t(15));
-    return L.total <= static_cast<size_t>(device_info().smem_optin);
+    const DeviceInfo di = device_info();
+    const size_t per_block = static_cast<size_t>(di.smem_per_sm / blocks_per_sm - di.smem_reserved);
+    return L.total <= std::min(per_block, static_cast<size_t>(di.smem_optin));
 }
 
 hepacc_status dispatch(hepacc_dtype kin, bool batched, const LaunchArgs& a) {
@@ -221,19 +223,24 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     B.n_samples = 1;
     make_sample(b, out, B.s[0]);
 
-    // the largest block (tile) whose layout fits, with block-private
-    // histograms when they fit, else with global ones
     const double lam_j = b->jets_per_event > 0 ? b->jets_per_event : 6.0;
     const double lam_l = b->leptons_per_event > 0 ? b->leptons_per_event : 1.5;
     const size_t kes = dtype_size(b->kin_type), bes = dtype_size(b->btag_type);
     Layout L;
     int E = 0, hmode = H_SMEM;
-    for (int e = kMaxThreads; e >= 128 && E == 0; e -= 32)
-        if (layout_for(e, H_SMEM, 1, lam_j, lam_l, kes, bes, P, L)) E = e;
-    if (E == 0) {
-        hmode = H_GLOBAL;
-        for (int e = kMaxThreads; e >= 32 && E == 0; e -= 32)
-            if (layout_for(e, H_GLOBAL, 1, lam_j, lam_l, kes, bes, P, L)) E = e;
+    // blocks per SM as built for, else one; the largest block that fits,
+    // with block-private histograms when they fit beside it, else global
+    // ones (smaller blocks measured slower than global histograms)
+    for (int bps = kMinBlocks; bps >= 1 && E == 0; bps = bps > 1 ? 1 : 0) {
+        for (int e = kMaxThreads; e >= 64 && E == 0; e -= 32) {
+            if (layout_for(e, H_SMEM, 1, lam_j, lam_l, kes, bes, bps, P, L)) {
+                E = e;
+                hmode = H_SMEM;
+            } else if (layout_for(e, H_GLOBAL, 1, lam_j, lam_l, kes, bes, bps, P, L)) {
+                E = e;
+                hmode = H_GLOBAL;
+            }
+        }
     }
     if (E == 0) return fail(HEPACC_ERR_INVALID_ARG, "chain stage buffers do not fit in shared memory");
 
@@ -274,7 +281,12 @@ struct hepacc_plan {
 namespace {
 
 hepacc_status plan_launch(const hepacc_plan* p, cudaStream_t s) {
-    for (const BatchDesc& B : p->launches) {
+    for (const BatchDesc& B0 : p->launches) {
+        // flat launches: the first tile of every sample for this block size
+        BatchDesc B = B0;
+        B.tile_start[0] = 0;
+        for (int i = 0; i < B.n_samples; ++i)
+            B.tile_start[i + 1] = B.tile_start[i] + (B.s[i].n + p->block - 1) / p->block;
         LaunchArgs a;
         a.layout = p->L;
         a.P = &p->P;
@@ -286,7 +298,8 @@ hepacc_status plan_launch(const hepacc_plan* p, cudaStream_t s) {
         a.block = p->block;
         a.cluster = p->cluster;
         a.grid = 0;
-        a.max_tiles = std::max<int64_t>(1, (p->max_events + p->block - 1) / p->block);
+        a.max_tiles = std::max<int64_t>(1, p->hmode == H_GLOBAL ? B.tile_start[B.n_samples]
+                                                               : (p->max_events + p->block - 1) / p->block);
         a.stream = s;
         const hepacc_status st = dispatch(p->kin, true, a);
         if (st != HEPACC_OK) return st;
@@ -431,10 +444,13 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
                              {H_CLUSTER, 8, HEPACC_PLAN_HIST_CLUSTER8},
                              {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16},
                              {H_GLOBAL, 1, HEPACC_PLAN_HIST_GLOBAL}};
-    for (const auto& m : modes)
-        for (int e = kMaxThreadsBatched; e >= 128 && (allowed & m[2]); e -= 32) {
+    for (const auto& m : modes) {
+        // flat launches (global histograms) take the single-sample block shape
+        const int emax = m[0] == H_GLOBAL ? kMaxThreads : kMaxThreadsBatched;
+        const int bps = m[0] == H_GLOBAL ? kMinBlocks : kMinBlocksBatched;
+        for (int e = emax; e >= 64 && (allowed & m[2]); e -= 32) {
             Candidate c;
-            if (layout_for(e, m[0], m[1], lam_j, lam_l, kes, bes, p->P, c.L)) {
+            if (layout_for(e, m[0], m[1], lam_j, lam_l, kes, bes, bps, p->P, c.L)) {
                 c.hmode = m[0];
                 c.cluster = m[1];
                 c.block = e;
@@ -442,6 +458,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
                 break;
             }
         }
+    }
     if (cands.empty()) return drop(fail(HEPACC_ERR_INVALID_ARG, "no chain layout fits in shared memory"));
     p->n_candidates = static_cast<int>(cands.size());
     p->tuned_ms = -1.0f;

@@ -46,13 +46,17 @@ constexpr int NC = 15;            // staged columns
 constexpr int kNV = HEPACC_CHAIN_NVARS;
 constexpr int kQ = kNV + 1;       // fill entry: 20 variables + variation
 constexpr int kScratch = 10;      // selected jets ranked from a queue slot (2 x 10 words of it)
-// Largest block of each launch form. Register allocation rounds a block of
-// 320 threads up like one of 384, which caps a thread at 168 registers; 256
-// threads allow 255. Single-sample launches run more warps per SM at 168
-// (some spilling); batched launches, whose loop over samples and pair work
-// keep more live state, run spill-free at 256.
-constexpr int kMaxThreads = 320;
+// Block shape of each launch form: threads per block (the largest tile) and
+// blocks per SM, measured best on GB300. Register allocation rounds blocks
+// up (160 threads count like 192, 320 like 384), so two blocks of 160 cap a
+// thread at 168 registers (some spilling) and one block of 256 at 255.
+// Single-sample launches run two independent 160-thread blocks per SM (a
+// stalled stage refill in one leaves the other running); batched launches,
+// with their loop over samples, run spill-free in one 256-thread block.
+constexpr int kMaxThreads = 160;
+constexpr int kMinBlocks = 2;
 constexpr int kMaxThreadsBatched = 256;
+constexpr int kMinBlocksBatched = 1;
 constexpr int kHdr = 96;          // stage header: spans, staged flag, column offsets
 constexpr int kEvWords = 12;      // event summary handed to the pairs
 
@@ -97,7 +101,14 @@ struct SampleDesc {
 struct BatchDesc {
     int n_samples;
     SampleDesc s[kMaxSamples];
+    int64_t tile_start[kMaxSamples + 1];   // F_FLAT: first flat tile of each sample (and the total)
 };
+
+// Launch forms: one sample; several samples walked in turn by every block
+// (histograms in block or cluster shared memory, flushed per sample); or
+// several samples as one flat sequence of tiles (global histograms: every
+// tile finds its sample, every record carries it).
+enum : int { F_SINGLE = 0, F_SAMPLES = 1, F_FLAT = 2 };
 
 // Histogram placement: block-private shared memory, global memory, or
 // spread over the shared memory of a thread-block cluster (each block owns
@@ -184,10 +195,14 @@ __device__ __forceinline__ void put4(uint32_t* q, float a, float b, float c, flo
     q[3] = __float_as_uint(d);
 }
 
-template <typename KT, typename BT, typename OffT, bool DEBUG, int HMODE, bool MULTI>
-__global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k_chain(const __grid_constant__ Layout L,
+template <typename KT, typename BT, typename OffT, bool DEBUG, int HMODE, int FORM>
+__global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxThreads,
+                                  FORM == F_SAMPLES ? kMinBlocksBatched : kMinBlocks) k_chain(const __grid_constant__ Layout L,
                                                           const __grid_constant__ ChainParams P,
                                                           const __grid_constant__ BatchDesc B) {
+    constexpr bool MULTI = FORM == F_SAMPLES;
+    constexpr bool FLAT = FORM == F_FLAT;
+    static_assert(!FLAT || HMODE == H_GLOBAL, "flat batched launches fill global histograms");
     unsigned char* smem = g_dyn_smem;
     const int tid = threadIdx.x;
     const int E = blockDim.x;
@@ -238,30 +253,51 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
     // sample's descriptor to shared memory at the top of the sample loop
     // (its fields are then read where they are used instead of occupying
     // registers for the whole sample).
+    // Flat launches read the descriptor of each tile's own sample.
     SampleDesc* cur = reinterpret_cast<SampleDesc*>(smem + L.sample);
-    auto SD = [&]() -> const SampleDesc& {
+    auto SDs = [&](int s) -> const SampleDesc& {
         if constexpr (MULTI)
             return *cur;
+        else if constexpr (FLAT)
+            return B.s[s];
         else
             return B.s[0];
     };
-    auto offs = [&](int c) { return static_cast<const OffT*>(SD().off[c]); };
     int64_t n = 0;
     int64_t ntiles = 0;
     const int64_t grid = gridDim.x;
+    // sample and tile within the sample of launch tile t (flat launches:
+    // the last sample whose first tile is at or before t)
+    auto where = [&](int64_t t, int& ts, int64_t& lt) {
+        if constexpr (FLAT) {
+            int k = 0;
+            for (int j = 1; j < B.n_samples; ++j) k = B.tile_start[j] <= t ? j : k;
+            ts = k;
+            lt = t - B.tile_start[k];
+        } else {
+            ts = 0;
+            lt = t;
+        }
+    };
 
     // thread 0: first and last element of every collection in tile tt
     auto load_span = [&](int64_t tt, int64_t (&S)[3], int64_t (&T)[3]) {
-        const int64_t a = tt * E;
-        const int64_t z = a + E < n ? a + E : n;
+        int ts;
+        int64_t lt;
+        where(tt, ts, lt);
+        const int64_t ns = SDs(ts).n;
+        const int64_t a = lt * E;
+        const int64_t z = a + E < ns ? a + E : ns;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            S[c] = ldoff(offs(c), a);
-            T[c] = ldoff(offs(c), z);
+            S[c] = ldoff(static_cast<const OffT*>(SDs(ts).off[c]), a);
+            T[c] = ldoff(static_cast<const OffT*>(SDs(ts).off[c]), z);
         }
     };
-    // thread 0: header of stage b and the bulk copies of the tile's spans
-    auto issue = [&](int b, const int64_t (&S)[3], const int64_t (&T)[3]) {
+    // thread 0: header of stage b and the bulk copies of the spans of tile
+    // tt (sample ts)
+    auto issue = [&](int b, int ts, const int64_t (&S)[3], const int64_t (&T)[3]) {
+        const SampleDesc& sd = SDs(ts);
         unsigned char* st = smem + b * L.stage_bytes;
         int64_t* hdr = reinterpret_cast<int64_t*>(st);
         uint32_t* hoff = reinterpret_cast<uint32_t*>(st + 32);
@@ -270,7 +306,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const ColSpec& cs = L.col[c];
-            const uintptr_t cb = reinterpret_cast<uintptr_t>(SD().col[c]);
+            const uintptr_t cb = reinterpret_cast<uintptr_t>(sd.col[c]);
             const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
             const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
             const uintptr_t bytes = T[cs.coll] > S[cs.coll] ? ((z + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)) : 0;
@@ -289,7 +325,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
             for (int c = 0; c < NC; ++c) {
                 const ColSpec& cs = L.col[c];
                 if (T[cs.coll] <= S[cs.coll]) continue;
-                const uintptr_t cb = reinterpret_cast<uintptr_t>(SD().col[c]);
+                const uintptr_t cb = reinterpret_cast<uintptr_t>(sd.col[c]);
                 const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
                 const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
                 const uintptr_t a16 = a & ~uintptr_t(15);
@@ -303,9 +339,9 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
 
     // Masses and fill for this warp's queued records [0, m) (warp-uniform).
     auto flush = [&](int m) {
-        const ChainOut& out = SD().out;
         const uint32_t* r = my_q + lane * R_WORDS;   // this lane's record
         const bool have = lane < m;
+        const ChainOut& out = SDs(have ? static_cast<int>((r[R_K] >> 9) & 0x7fu) : 0).out;
         float var[kNV];
         int k = 0;
         bool pass = false;
@@ -451,6 +487,22 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
     uint32_t uses[2] = {0u, 0u};   // thread 0: copies issued into each stage
     int b = 0;
     bool stop = false;   // a bounded wait gave up: skip the remaining work, keep the barriers
+    // this thread's offsets and weight of tile t (loaded a tile ahead)
+    auto own_offsets = [&](int64_t t, int64_t (&os)[3], int64_t (&ot)[3], float& w) {
+        int ts;
+        int64_t lt;
+        where(t, ts, lt);
+        const SampleDesc& sd = SDs(ts);
+        const int64_t ns = sd.n;
+        const int64_t e = lt * E + tid;
+        const int64_t elo = e < ns ? e : ns, ehi = e + 1 < ns ? e + 1 : ns;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            os[c] = ldoff(static_cast<const OffT*>(sd.off[c]), elo);
+            ot[c] = ldoff(static_cast<const OffT*>(sd.off[c]), ehi);
+        }
+        w = e < ns ? sd.weight[e] : 0.0f;
+    };
     for (int sl = 0; sl < (MULTI ? B.n_samples : 1); ++sl) {
     if constexpr (MULTI) {
         __syncthreads();   // every warp is done with the previous descriptor
@@ -458,10 +510,15 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
             reinterpret_cast<uint64_t*>(cur)[i] = reinterpret_cast<const uint64_t*>(&B.s[sl])[i];
         __syncthreads();
     }
-    n = SD().n;
-    ntiles = (n + E - 1) / E;
+    if constexpr (FLAT) {
+        ntiles = B.tile_start[B.n_samples];
+    } else {
+        n = SDs(0).n;
+        ntiles = (n + E - 1) / E;
+    }
     int64_t tile = stop ? ntiles : blockIdx.x;
     int64_t cs_[3] = {0, 0, 0}, ct_[3] = {0, 0, 0};
+    float cw_ = 0.0f;   // this thread's event weight, loaded a tile ahead like its offsets
     if (tile < ntiles) {
         if (tid == 0) {
             int64_t S0[3], T0[3];
@@ -470,18 +527,15 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
             bool ok = true;
             if (uses[b] > 0) ok = mbar_wait_bounded(empty[b], (uses[b] - 1) & 1u);
             if (ok) {
-                issue(b, S0, T0);
+                int ts;
+                int64_t lt;
+                where(tile, ts, lt);
+                issue(b, ts, S0, T0);
                 ++uses[b];
             }
             if (tile + grid < ntiles) load_span(tile + grid, S1, T1);
         }
-        const int64_t e = tile * E + tid;
-        const int64_t elo = e < n ? e : n, ehi = e + 1 < n ? e + 1 : n;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cs_[c] = ldoff(offs(c), elo);
-            ct_[c] = ldoff(offs(c), ehi);
-        }
+        own_offsets(tile, cs_, ct_, cw_);
     }
     for (; tile < ntiles; tile += grid) {
         const int64_t next = tile + grid;
@@ -490,22 +544,18 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
             bool ok = true;
             if (uses[b ^ 1] > 0) ok = mbar_wait_bounded(empty[b ^ 1], (uses[b ^ 1] - 1) & 1u);
             if (ok) {
-                issue(b ^ 1, S1, T1);
+                int ts;
+                int64_t lt;
+                where(next, ts, lt);
+                issue(b ^ 1, ts, S1, T1);
                 ++uses[b ^ 1];
                 if (next + grid < ntiles) load_span(next + grid, S1, T1);
             }
         }
         __syncwarp();
         int64_t ns_[3] = {0, 0, 0}, nt_[3] = {0, 0, 0};
-        if (next < ntiles) {
-            const int64_t e = next * E + tid;
-            const int64_t elo = e < n ? e : n, ehi = e + 1 < n ? e + 1 : n;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                ns_[c] = ldoff(offs(c), elo);
-                nt_[c] = ldoff(offs(c), ehi);
-            }
-        }
+        float nw_ = 0.0f;
+        if (next < ntiles) own_offsets(next, ns_, nt_, nw_);
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(full[b], fpar[b]))) {   // error word set; this warp stops
             stop = true;
             break;
@@ -515,7 +565,12 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
         const unsigned char* st = smem + b * L.stage_bytes;
         const int64_t* hdr = reinterpret_cast<const int64_t*>(st);
         const uint32_t* hoff = reinterpret_cast<const uint32_t*>(st + 32);
-        const int64_t e = tile * E + tid;
+        // this tile's sample and its first event within the sample
+        int cur_s;
+        int64_t ltile;
+        where(tile, cur_s, ltile);
+        if constexpr (FLAT) n = SDs(cur_s).n;
+        const int64_t e = ltile * E + tid;
         const bool valid = e < n;
         int rs[3], rt[3];
 #pragma unroll
@@ -527,7 +582,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
         StagedCols sc;
         DirectCols dc;
         dc.L = &L;
-        dc.base = SD().col;
+        dc.base = SDs(cur_s).col;
 #pragma unroll
         for (int c = 0; c < 3; ++c) dc.S[c] = hdr[c];
         if (staged) {
@@ -602,7 +657,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
             else
                 lep_vals(dc);
         }
-        if (DEBUG && valid && SD().out.ev_nlep) SD().out.ev_nlep[e] = nlep;
+        if (DEBUG && valid && SDs(0).out.ev_nlep) SDs(0).out.ev_nlep[e] = nlep;
         // without per-event outputs only single-lepton events can pass
         const bool active = valid && (DEBUG || nlep == 1);
         const unsigned amask = __ballot_sync(0xffffffffu, active);
@@ -829,7 +884,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
         my_evs[6 * 32 + lane] = static_cast<uint32_t>(nlep);
         my_evs[7 * 32 + lane] = __float_as_uint(leta);
         my_evs[8 * 32 + lane] = __float_as_uint(lphi);
-        my_evs[9 * 32 + lane] = __float_as_uint(valid ? SD().weight[e] : 0.0f);
+        my_evs[9 * 32 + lane] = __float_as_uint(cw_);
         my_evs[10 * 32 + lane] = __float_as_uint(lpt);
         my_evs[11 * 32 + lane] = __float_as_uint(liso);
         __syncwarp();
@@ -903,8 +958,8 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
                     write4(sc);
                 else
                     write4(dc);
-                r[R_E] = static_cast<uint32_t>(tile * E + warp * 32 + el);
-                r[R_K] = static_cast<uint32_t>(k) | (pass ? 0x100u : 0u) |
+                r[R_E] = static_cast<uint32_t>(ltile * E + warp * 32 + el);
+                r[R_K] = static_cast<uint32_t>(k) | (pass ? 0x100u : 0u) | (static_cast<uint32_t>(cur_s) << 9) |
                          (static_cast<uint32_t>(min(ev.nlep, 0xffff)) << 16);
                 r[R_NJ] = static_cast<uint32_t>(min(nsel, 0xffff)) | (static_cast<uint32_t>(min(nbj, 0xffff)) << 16);
                 r[R_W] = my_evs[9 * 32 + el];
@@ -947,6 +1002,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
             cs_[c] = ns_[c];
             ct_[c] = nt_[c];
         }
+        cw_ = nw_;
         b ^= 1;
     }
     if (qcount > 0) flush(qcount);
@@ -955,7 +1011,7 @@ __global__ void __launch_bounds__(MULTI ? kMaxThreadsBatched : kMaxThreads, 1) k
     // the sample's histograms: block-private or cluster-slice copies go to
     // the sample's outputs and are cleared for the next sample
     if (HMODE != H_GLOBAL) {
-        const ChainOut& out = SD().out;
+        const ChainOut& out = SDs(0).out;
         if (HMODE == H_CLUSTER)
             cluster_sync_all();
         else
@@ -1067,11 +1123,11 @@ hepacc_status run_typed(const LaunchArgs& a) {
         using BT = typename decltype(bt)::type;
         using O = typename decltype(ot)::type;
         if (a.debug) {
-            if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, true, H_SMEM, false>, a);
-            return launch_chain(k_chain<KT, BT, O, true, H_GLOBAL, false>, a);
+            if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, true, H_SMEM, F_SINGLE>, a);
+            return launch_chain(k_chain<KT, BT, O, true, H_GLOBAL, F_SINGLE>, a);
         }
-        if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, false, H_SMEM, false>, a);
-        return launch_chain(k_chain<KT, BT, O, false, H_GLOBAL, false>, a);
+        if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, false, H_SMEM, F_SINGLE>, a);
+        return launch_chain(k_chain<KT, BT, O, false, H_GLOBAL, F_SINGLE>, a);
     };
     auto with_o = [&](auto bt) -> hepacc_status {
         if (a.offsets_type == HEPACC_I32) return go(bt, Tag<int32_t>{});
@@ -1082,13 +1138,14 @@ hepacc_status run_typed(const LaunchArgs& a) {
 }
 
 // Many samples in one launch (int64 offsets; btag float32 with float32
-// kinematics, float16 with half kinematics).
+// kinematics, float16 with half kinematics): shared-memory histograms walk
+// the samples in turn, global ones run the samples as one flat tile range.
 template <typename KT, typename BT>
 hepacc_status run_batched_typed(const LaunchArgs& a) {
     if (a.offsets_type != HEPACC_I64) return fail(HEPACC_ERR_DTYPE, "batched launches need I64 offsets");
-    if (a.hmode == H_CLUSTER) return launch_chain(k_chain<KT, BT, int64_t, false, H_CLUSTER, true>, a);
-    if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, int64_t, false, H_SMEM, true>, a);
-    return launch_chain(k_chain<KT, BT, int64_t, false, H_GLOBAL, true>, a);
+    if (a.hmode == H_CLUSTER) return launch_chain(k_chain<KT, BT, int64_t, false, H_CLUSTER, F_SAMPLES>, a);
+    if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, int64_t, false, H_SMEM, F_SAMPLES>, a);
+    return launch_chain(k_chain<KT, BT, int64_t, false, H_GLOBAL, F_FLAT>, a);
 }
 
 hepacc_status run_f32(const LaunchArgs& a);

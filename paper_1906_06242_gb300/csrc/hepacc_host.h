@@ -22,6 +22,8 @@ struct DeviceInfo {
     int sms;
     int smem_optin;
     int max_threads_per_sm;
+    int smem_per_sm;      // shared memory of one SM
+    int smem_reserved;    // shared memory the runtime reserves per block
 };
 DeviceInfo device_info();
 

@@ -1,0 +1,75 @@
+"""Run one chain workload a few times (for profilers and quick timings).
+
+  python -m paper_1906_06242_gb300.workloads plain --events 2000000 --runs 3
+  python -m paper_1906_06242_gb300.workloads plain --events 2000000 --kin bf16
+  python -m paper_1906_06242_gb300.workloads batched --scale 0.02 --runs 3
+
+``plain``: one sample of the benchmark generator (int64 offsets), one
+variation, hepacc_run_chain. ``batched``: the 12-sample set with 21 jet-pt
+variations as one plan (no autotuning, no graph, so that every launch is a
+plain kernel launch); ``--placement`` picks the histogram placement. Prints
+the mean device time per run.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import numpy as np
+import torch
+
+from . import hepacc as H
+from . import synth
+
+PLACEMENTS = {"block": 4, "cluster8": 8, "cluster16": 16, "global": 32}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("workload", choices=["plain", "batched"])
+    p.add_argument("--events", type=int, default=2_000_000)
+    p.add_argument("--kin", choices=["f32", "bf16", "f16"], default="f32")
+    p.add_argument("--scale", type=float, default=0.02)
+    p.add_argument("--variations", type=int, default=21)
+    p.add_argument("--placement", choices=sorted(PLACEMENTS), default="global")
+    p.add_argument("--runs", type=int, default=3)
+    a = p.parse_args(argv)
+    H.load()
+    if a.workload == "plain":
+        batch = synth.generate(a.events, 1)
+        if a.kin != "f32":
+            batch = synth.reduced_precision(batch, a.kin)
+        cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [1.0])
+        db = H.DeviceBatch.from_host(batch)
+        out = H.ChainOutputs(cfg, batch.n_events)
+        st = (db.c_struct(), cfg.c_struct(), out.c_struct())
+
+        def run():
+            H.hepacc_run_chain(db, cfg, out, _structs=st)
+        n = batch.n_events
+    else:
+        samples = synth.batched_samples(12, size_scale=a.scale)
+        if a.kin != "f32":
+            samples = [synth.reduced_precision(s, a.kin) for s in samples]
+        shifts = synth.variation_shifts(a.variations)
+        cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [np.float32(1.0 + 0.01 * k) for k in shifts])
+        dbs = [H.DeviceBatch.from_host(s) for s in samples]
+        outs = [H.ChainOutputs(cfg, s.n_events) for s in samples]
+        plan = H.hepacc_plan_create(cfg, dbs, outs, flags=PLACEMENTS[a.placement])
+        run = plan.run
+        n = sum(s.n_events for s in samples)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(a.runs):
+        run()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / max(1, a.runs)
+    print(f"{a.workload} events={n} ms_per_run={ms:.3f} events_per_s={n / (ms * 1e-3):.4g} "
+          f"device_error={H.device_error()}")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
