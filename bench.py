@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the secondary forms")
     p.add_argument("--batched-scale", type=float, default=1.0,
                    help="size factor of the 12-sample batched set (1.0: 0.2M to 20M events per sample)")
+    p.add_argument("--dense-events", type=int, default=60_000_000,
+                   help="events of the dense scale set (12 jets, 2.5 muons per event); 0 skips it")
     return p.parse_args()
 
 
@@ -307,6 +309,8 @@ def main():
     if not args.no_extra and rank == 0:
         extra = secondary_forms(H, synth, batch, torch, stream)
         extra.update(batched_forms(H, synth, torch, stream, args.batched_scale))
+        if args.dense_events > 0:
+            extra.update(dense_forms(H, synth, torch, stream, args.dense_events))
 
     if rank != 0:
         if dist:
@@ -402,7 +406,7 @@ def batched_forms(H, synth, torch, stream, scale):
     separate per-operation library calls."""
     import numpy as np
     t0 = time.perf_counter()
-    samples = synth.batched_samples(12, size_scale=scale)
+    samples = synth.batched_samples(12, size_scale=scale, workers=min(12, os.cpu_count() or 1))
     gen_s = time.perf_counter() - t0
     n_tot = sum(s.n_events for s in samples)
     shifts = synth.variation_shifts(N_VARIATIONS_BATCHED)
@@ -468,6 +472,87 @@ def batched_forms(H, synth, torch, stream, scale):
                                  "speedup_vs_fused_calls": res["plain_calls_12x21"]["ms_per_step"] / ms,
                                  "speedup_vs_per_op_calls": res["per_op_calls_12x21"]["ms_per_step"] / ms}
     plan.close()
+    return res
+
+
+def dense_forms(H, synth, torch, stream, n_events):
+    """The scale form: dense events (Poisson 12 jets, 2.5 muons, 0.8
+    electrons; drawn in 5M-event chunks from seed 5) resident in HBM as FP32
+    and as BF16 columns, and the FP32 set streamed from pinned host memory
+    in 2 GB batches on a copy stream overlapped with the chain."""
+    import numpy as np
+    from paper_1906_06242_gb300 import streaming
+    t0 = time.perf_counter()
+    w = synth.WORKLOADS["scale_60m"]
+    b = synth.generate_chunked(n_events, w["seed"], chunk=5_000_000, workers=min(12, os.cpu_count() or 1),
+                               lam_jet=w["lam_jet"], lam_mu=w["lam_mu"], lam_el=w["lam_el"],
+                               offset_dtype=np.int64)
+    gen_s = time.perf_counter() - t0
+    cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [1.0])
+    hbm, _ = peaks()
+
+    def timeit(fn, k, w=2):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / k
+
+    res = {}
+
+    def resident(batch, name):
+        db = H.DeviceBatch.from_host(batch)
+        out = H.ChainOutputs(cfg, batch.n_events)
+        st = (db.c_struct(), cfg.c_struct(), out.c_struct())
+        ms = timeit(lambda: H.hepacc_run_chain(db, cfg, out, stream=stream, _structs=st), k=10)
+        nbytes = db.nbytes_read()
+        out.zero_()
+        H.hepacc_run_chain(db, cfg, out, stream=stream, _structs=st)
+        res[name] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms,
+                     "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9, "algorithmic_bytes": int(nbytes),
+                     "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "events": int(batch.n_events)}
+        return out
+
+    ref = resident(b, "dense_resident_f32")
+    ref_counts = ref.counts.clone()
+    del ref
+    torch.cuda.empty_cache()
+    out = H.ChainOutputs(cfg, b.n_events)
+    t0 = time.perf_counter()
+    sc = streaming.StreamedChain(b, cfg, out, batch_bytes=2 << 30)
+    pin_s = time.perf_counter() - t0
+    ms = timeit(lambda: sc.run(stream), k=3, w=1)
+    # the two halves alone: copies (copy stream), chain (buffers as they are)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(sc.copy_stream)
+    sc.run_copies()
+    e.record(sc.copy_stream)
+    torch.cuda.synchronize()
+    copy_ms = a.elapsed_time(e)
+    compute_ms = timeit(lambda: sc.run_compute(stream), k=2, w=1)
+    out.zero_()
+    sc.run(stream)
+    torch.cuda.synchronize()
+    res["dense_streamed_f32"] = {"events_per_s": b.n_events / (ms * 1e-3), "ms_per_step": ms,
+                                 "h2d_bytes_per_step": int(sc.h2d_bytes),
+                                 "h2d_gbs": sc.h2d_bytes / (ms * 1e-3) / 1e9, "batches": len(sc.ranges),
+                                 "batch_bytes": 2 << 30, "pinning_s": pin_s,
+                                 "copies_only_ms": copy_ms, "copies_only_gbs": sc.h2d_bytes / (copy_ms * 1e-3) / 1e9,
+                                 "chain_only_ms": compute_ms,
+                                 "overlap": max(copy_ms, compute_ms) / ms,
+                                 "counts_equal_resident": bool(torch.equal(out.counts, ref_counts))}
+    del sc, out
+    torch.cuda.empty_cache()
+    hb = synth.reduced_precision(b, "bf16")
+    del b
+    resident(hb, "dense_resident_bf16")
+    res["dense_resident_bf16"]["generation_s"] = gen_s
     return res
 
 

@@ -245,24 +245,73 @@ def reduced_precision(batch: EventBatch, kin_fmt: str, btag_fmt: str = "f16") ->
 WORKLOADS = {
     "plain_100k": dict(n_events=100_000, seed=1, offset_dtype=np.int32),
     "plain_10m": dict(n_events=10_000_000, seed=1, offset_dtype=np.int64),
+    # drawn in chunks (generate_chunked), so that it can be generated in parallel
     "scale_60m": dict(n_events=60_000_000, seed=5, offset_dtype=np.int64,
                       lam_jet=12.0, lam_mu=2.5, lam_el=0.8),
 }
 
 
+def _one_sample(i: int, first_seed: int, lo: float, hi: float, size_scale: float) -> EventBatch:
+    rng = np.random.default_rng(first_seed + i)
+    size = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+    size = max(0, int(round(size * size_scale)))
+    return generate(size, first_seed + i, rng=rng, offset_dtype=np.int64)
+
+
+def _pool(workers: int):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
 def batched_samples(n_samples: int = 12, first_seed: int = 11, lo: float = 2e5,
-                    hi: float = 2e7, size_scale: float = 1.0):
+                    hi: float = 2e7, size_scale: float = 1.0, workers: int = 1):
     """The uneven-size sample set: sample i uses ``default_rng(first_seed + i)``;
     its first draw fixes its size round(exp(U(ln lo, ln hi))) (times
     ``size_scale``, for reduced test versions), and the events follow from the
-    same generator."""
-    out = []
-    for i in range(n_samples):
-        rng = np.random.default_rng(first_seed + i)
-        size = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
-        size = max(0, int(round(size * size_scale)))
-        out.append(generate(size, first_seed + i, rng=rng, offset_dtype=np.int64))
-    return out
+    same generator. ``workers`` > 1 draws the samples in that many spawned
+    processes (same arrays)."""
+    args = [(i, first_seed, lo, hi, size_scale) for i in range(n_samples)]
+    if workers <= 1:
+        return [_one_sample(*a) for a in args]
+    with _pool(workers) as ex:
+        return list(ex.map(_one_sample, *zip(*args)))
+
+
+def _one_chunk(n: int, seed: int, i: int, kw: dict) -> EventBatch:
+    return generate(n, seed, rng=np.random.default_rng([seed, i]), **kw)
+
+
+def concat_batches(parts) -> EventBatch:
+    """Events of ``parts`` one after the other (offsets rebased)."""
+    n = sum(p.n_events for p in parts)
+    offsets = {}
+    for coll in ("jet", "mu", "el"):
+        dt = parts[0].offsets[coll].dtype
+        off = np.zeros(n + 1, dtype=np.int64)
+        at, base = 0, 0
+        for p in parts:
+            o = p.offsets[coll].astype(np.int64)
+            off[at + 1:at + p.n_events + 1] = o[1:] - o[0] + base
+            at += p.n_events
+            base += int(o[-1] - o[0])
+        offsets[coll] = off.astype(dt)
+    cols = {k: np.concatenate([p.cols[k] for p in parts]) for k in parts[0].cols}
+    return EventBatch(n_events=n, jet_offsets=offsets["jet"], mu_offsets=offsets["mu"], el_offsets=offsets["el"],
+                      cols=cols, weight=np.concatenate([p.weight for p in parts]), seed=parts[0].seed)
+
+
+def generate_chunked(n_events: int, seed: int, chunk: int = 5_000_000, workers: int = 1, **kw) -> EventBatch:
+    """``n_events`` events drawn as consecutive chunks of ``chunk`` events,
+    chunk i from ``default_rng([seed, i])`` with the recipe of ``generate``
+    (the large scale set, so that its chunks can be drawn in parallel)."""
+    sizes = [min(chunk, n_events - a) for a in range(0, n_events, chunk)]
+    if workers <= 1:
+        parts = [_one_chunk(m, seed, i, kw) for i, m in enumerate(sizes)]
+    else:
+        with _pool(workers) as ex:
+            parts = list(ex.map(_one_chunk, sizes, [seed] * len(sizes), range(len(sizes)), [kw] * len(sizes)))
+    return concat_batches(parts) if parts else generate(0, seed, **kw)
 
 
 def hand_batch(events, offset_dtype=np.int64) -> EventBatch:
