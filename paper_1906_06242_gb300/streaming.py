@@ -116,20 +116,27 @@ class StreamedChain:
     def h2d_bytes(self) -> int:
         return sum(t.numel() * t.element_size() for p in self.parts for t in p.values())
 
-    def run_copies(self):
-        """The copies of one pass alone (on the copy stream)."""
-        torch = self.torch
-        for i, (p, (v, _, _)) in enumerate(zip(self.parts, self.views)):
-            with torch.cuda.stream(self.copy_stream):
-                for k, t in p.items():
-                    v[k].copy_(t, non_blocking=True)
-
-    def run_compute(self, stream=None):
-        """The chain of one pass alone, on whatever the buffers hold."""
+    def run_serial(self, stream=None):
+        """One pass with no overlap (each range copied, then its chain, on
+        one stream); returns the milliseconds spent in copies and in the
+        chain. For measurement only."""
         torch = self.torch
         compute = stream if stream is not None else torch.cuda.current_stream()
-        for _, db, structs in self.views:
+        marks = []
+        for p, (v, db, structs) in zip(self.parts, self.views):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(compute)
+            with torch.cuda.stream(compute):
+                for k, t in p.items():
+                    v[k].copy_(t, non_blocking=True)
+            e1.record(compute)
             H.hepacc_run_chain(db, self.cfg, self.out, stream=compute, _structs=structs)
+            e2.record(compute)
+            marks.append((e0, e1, e2))
+        torch.cuda.synchronize()
+        copy_ms = sum(a.elapsed_time(b) for a, b, _ in marks)
+        chain_ms = sum(b.elapsed_time(c) for _, b, c in marks)
+        return copy_ms, chain_ms
 
     def run(self, stream=None):
         """One pass over the whole batch; enqueued on ``stream`` (default:
