@@ -499,6 +499,145 @@ void oracle_max_pt_trijet(const void *pt, const void *eta, const void *phi, cons
 }
 
 /* ---------------------------------------------------------------------------
+ * Top-quark candidate (Section IV: the jet triplet with invariant mass
+ * closest to the top mass), FP64
+ * ------------------------------------------------------------------------- */
+
+/* Per event with mask_rows set: among triplets i<j<k of masked-in objects,
+ * the one whose mass (FP64) is closest to target; ties go to the first in
+ * lexicographic order. out_mass its mass, out_idx3 the local indices,
+ * out_gap = |m_runner_up - target| - |m_best - target| (+inf with one
+ * triplet). Fewer than three objects: NaN and -1 -1 -1. */
+void oracle_trijet_closest_mass(const void *pt, const void *eta, const void *phi, const void *mass, int t,
+                                const void *off, int ot, int64_t n, const uint8_t *mask_rows,
+                                const uint8_t *mask_content, double target, double *out_mass,
+                                int32_t *out_idx3, double *out_gap)
+{
+    for (int64_t ev = 0; ev < n; ev++) {
+        if (!on(mask_rows, ev))
+            continue;
+        int64_t i0 = get_off(off, ot, ev), i1 = get_off(off, ot, ev + 1);
+        double best_d = INFINITY, second_d = INFINITY, best_m = NAN;
+        int64_t bi = -1, bj = -1, bk = -1, ntrip = 0;
+        for (int64_t i = i0; i < i1; i++) {
+            if (!on(mask_content, i))
+                continue;
+            for (int64_t j = i + 1; j < i1; j++) {
+                if (!on(mask_content, j))
+                    continue;
+                for (int64_t k = j + 1; k < i1; k++) {
+                    if (!on(mask_content, k))
+                        continue;
+                    double p3[3] = {get_f(pt, t, i), get_f(pt, t, j), get_f(pt, t, k)};
+                    double e3[3] = {get_f(eta, t, i), get_f(eta, t, j), get_f(eta, t, k)};
+                    double f3[3] = {get_f(phi, t, i), get_f(phi, t, j), get_f(phi, t, k)};
+                    double m3[3] = {get_f(mass, t, i), get_f(mass, t, j), get_f(mass, t, k)};
+                    double m = oracle_mass3(p3, e3, f3, m3);
+                    double d = fabs(m - target);
+                    ntrip++;
+                    if (d < best_d) {
+                        second_d = best_d;
+                        best_d = d;
+                        best_m = m;
+                        bi = i - i0; bj = j - i0; bk = k - i0;
+                    } else if (d < second_d) {
+                        second_d = d;
+                    }
+                }
+            }
+        }
+        if (out_mass) out_mass[ev] = ntrip ? best_m : NAN;
+        if (out_idx3) {
+            out_idx3[3 * ev] = (int32_t)bi;
+            out_idx3[3 * ev + 1] = (int32_t)bj;
+            out_idx3[3 * ev + 2] = (int32_t)bk;
+        }
+        if (out_gap) out_gap[ev] = ntrip > 1 ? second_d - best_d : INFINITY;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * select_opposite_sign_muons (Section III, specialised kernels)
+ * ------------------------------------------------------------------------- */
+
+/* Per event with mask_rows set: over the masked-in objects in stored order
+ * (the data's pt order), the first i that has a later masked-in j of
+ * opposite charge (charge[i] * charge[j] < 0), with the first such j.
+ * mask_out is 1 for those two and 0 for every other object of the event
+ * (all 0 without such a pair). Events with mask_rows unset are untouched. */
+void oracle_select_opposite_sign(const int8_t *charge, const void *off, int ot, int64_t n,
+                                 const uint8_t *mask_rows, const uint8_t *mask_in, uint8_t *mask_out)
+{
+    for (int64_t ev = 0; ev < n; ev++) {
+        if (!on(mask_rows, ev))
+            continue;
+        int64_t i0 = get_off(off, ot, ev), i1 = get_off(off, ot, ev + 1);
+        int64_t a = -1, b = -1;
+        for (int64_t i = i0; i < i1 && a < 0; i++) {
+            if (!on(mask_in, i))
+                continue;
+            for (int64_t j = i + 1; j < i1; j++) {
+                if (on(mask_in, j) && (int)charge[i] * (int)charge[j] < 0) {
+                    a = i;
+                    b = j;
+                    break;
+                }
+            }
+        }
+        for (int64_t i = i0; i < i1; i++)
+            mask_out[i] = (uint8_t)(i == a || i == b);
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * get_bin_contents (Section III kernel list): histogram lookup
+ * ------------------------------------------------------------------------- */
+
+/* out[j] = contents[b] with b the bin of x[j] (bin_of; contents has nbins+2
+ * entries, under- and overflow included); NaN for NaN input. With
+ * interpolate set: linear interpolation between the contents of
+ * neighbouring in-range bins at their centres c_b = (e[b-1] + e[b]) * 0.5,
+ * clamped to the first and last in-range bin outside [c_1, c_nbins]. All in
+ * binary32, every operation rounded (no contraction): for c_b <= v < c_b+1,
+ * t = (v - c_b) / (c_b+1 - c_b) and out = y_b + t * (y_b+1 - y_b). */
+void oracle_get_bin_contents(const void *x, int xt, int64_t m, const float *edges, int nbins,
+                             const float *contents, int interpolate, float *out)
+{
+    for (int64_t j = 0; j < m; j++) {
+        float v = get_f(x, xt, j);
+        if (isnan(v)) {
+            out[j] = NAN;
+            continue;
+        }
+        if (!interpolate) {
+            out[j] = contents[bin_of((double)v, edges, nbins)];
+            continue;
+        }
+        float c1 = (edges[0] + edges[1]) * 0.5f;
+        float cn = (edges[nbins - 1] + edges[nbins]) * 0.5f;
+        if (nbins == 1 || v < c1) {
+            out[j] = contents[1];
+            continue;
+        }
+        if (v >= cn) {
+            out[j] = contents[nbins];
+            continue;
+        }
+        for (int b = 1; b < nbins; b++) {
+            float cb = (edges[b - 1] + edges[b]) * 0.5f;
+            float cb1 = (edges[b] + edges[b + 1]) * 0.5f;
+            if (v >= cb && v < cb1) {
+                float tt = (v - cb) / (cb1 - cb);
+                float d = contents[b + 1] - contents[b];
+                float prod = tt * d;
+                out[j] = contents[b] + prod;
+                break;
+            }
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
  * The benchmark chain (Section IV), one plain loop per variation and event
  * ------------------------------------------------------------------------- */
 

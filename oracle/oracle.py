@@ -87,7 +87,9 @@ def _p(a):
     if a is None:
         return None
     assert a.flags["C_CONTIGUOUS"], "oracle inputs must be contiguous"
-    return ctypes.c_void_p(a.ctypes.data)
+    # the returned pointer keeps the array alive (masks converted on the fly
+    # are temporaries)
+    return a.ctypes.data_as(ctypes.c_void_p)
 
 
 def _code(a, fmt=None):
@@ -292,6 +294,46 @@ class _Outputs(ctypes.Structure):
                 ("ev_pass", ctypes.c_void_p), ("ev_nlep", ctypes.c_void_p),
                 ("ev_njet", ctypes.c_void_p), ("ev_nb", ctypes.c_void_p), ("ev_idx", ctypes.c_void_p),
                 ("ev_vars", ctypes.c_void_p), ("ev_gap", ctypes.c_void_p), ("ev_idx2", ctypes.c_void_p)]
+
+
+def trijet_closest_mass(pt, eta, phi, mass, offsets, target=172.0, mask_rows=None, mask_content=None, fmt=None):
+    """Per event: the triplet of masked-in objects whose FP64 mass is closest
+    to ``target`` (Section IV top candidate). Returns (mass, idx3 [N,3],
+    gap) with gap = |m_second - target| - |m_best - target|."""
+    n = len(offsets) - 1
+    m = np.full(n, np.nan)
+    idx = np.full((n, 3), -7, dtype=np.int32)
+    gap = np.full(n, np.nan)
+    L = lib()
+    L.oracle_trijet_closest_mass(_p(pt), _p(eta), _p(phi), _p(mass), _code(pt, fmt), _p(offsets), _code(offsets),
+                                 _i64(n), _p(_u8(mask_rows)), _p(_u8(mask_content)), ctypes.c_double(target),
+                                 _p(m), _p(idx), _p(gap))
+    return m, idx, gap
+
+
+def select_opposite_sign(charge, offsets, mask_rows=None, mask_in=None, out=None):
+    """Per event: keep the first two masked-in objects of opposite charge
+    (Section III specialised kernel); ``out`` (uint8, content size) is
+    written only for events with mask_rows set."""
+    n = len(offsets) - 1
+    charge = np.ascontiguousarray(charge, dtype=np.int8)
+    if out is None:
+        out = np.zeros(len(charge), dtype=np.uint8)
+    lib().oracle_select_opposite_sign(_p(charge), _p(offsets), _code(offsets), _i64(n), _p(_u8(mask_rows)),
+                                      _p(_u8(mask_in)), _p(out))
+    return out
+
+
+def get_bin_contents(x, edges, contents, interpolate=False, fmt=None):
+    """Lookup of ``contents`` (nbins+2 float32, under/overflow included) at
+    the bins of ``x`` (Section III kernel list), or the binary32 linear
+    interpolation between bin centres."""
+    edges = np.ascontiguousarray(edges, dtype=np.float32)
+    contents = np.ascontiguousarray(contents, dtype=np.float32)
+    out = np.empty(len(x), dtype=np.float32)
+    lib().oracle_get_bin_contents(_p(x), _code(x, fmt), _i64(len(x)), _p(edges), ctypes.c_int(len(edges) - 1),
+                                  _p(contents), ctypes.c_int(1 if interpolate else 0), _p(out))
+    return out
 
 
 def run_chain(batch, cuts, hist_specs, shifts, per_event=True, kin_fmt=None, btag_fmt=None):

@@ -32,6 +32,12 @@ MUTATIONS = [
     ("HT in FP64", "ht += ptk;", "ht = (float)((double)ht + (double)ptk + 1e-7 * ptk);"),
     ("weight squared missing", "o->sumw2[at] += w * w;", "o->sumw2[at] += w;"),
     ("set writes next", "((uint8_t *)x)[i] = (uint8_t)value;", "((uint8_t *)x)[i + 1] = (uint8_t)value;"),
+    ("closest mass tie keeps last", "if (d < best_d) {", "if (d <= best_d) {"),
+    ("closest mass uses max", "double d = fabs(m - target);", "double d = -fabs(m - target);"),
+    ("opposite sign is different", "(int)charge[i] * (int)charge[j] < 0", "charge[i] != charge[j]"),
+    ("opposite sign ignores mask", "if (on(mask_in, j) && ", "if ("),
+    ("lookup interpolates from the upper bin", "out[j] = contents[b] + prod;", "out[j] = contents[b + 1] - prod;"),
+    ("lookup centre is the lower edge", "float cb = (edges[b - 1] + edges[b]) * 0.5f;", "float cb = edges[b - 1];"),
 ]
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

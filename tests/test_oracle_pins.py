@@ -583,3 +583,146 @@ def test_chain_dr2_equal_to_cut_keeps_jet(orc):
     out = orc.run_chain(synth.hand_batch(evs), synth.CUTS, synth.HIST_SPECS, [0])
     assert list(out["njet"][0]) == [2, 1]
     assert list(out["pass"][0]) == [1, 0]
+
+
+# --- next rows: top candidate closest to the top mass, opposite-sign muons,
+# --- histogram lookups (Sections III and IV)
+
+def _closest_brute(pt, eta, phi, mass, off, target):
+    """Per event: (mass, local indices, gap) of the triplet whose pairwise-
+    formula mass is closest to target; combinations are lexicographic, so a
+    strict comparison keeps the first on ties."""
+    res = []
+    for e in range(len(off) - 1):
+        a, b = int(off[e]), int(off[e + 1])
+        objs = [(float(pt[i]), float(eta[i]), float(phi[i]), float(mass[i])) for i in range(a, b)]
+        best = None
+        for c in itertools.combinations(range(len(objs)), 3):
+            m = _pairwise_mass([objs[i] for i in c])
+            d = abs(m - target)
+            if best is None or d < best[0]:
+                best = (d, m, c)
+        res.append(best)
+    return res
+
+
+def test_trijet_closest_mass_brute_force(orc):
+    rng = np.random.default_rng(31)
+    n = 300
+    _, off = _jagged(rng, n, 5.0)
+    m = int(off[-1])
+    pt = (20 + rng.exponential(60, m)).astype(np.float32)
+    eta = rng.normal(0, 1.5, m).astype(np.float32)
+    phi = rng.uniform(-np.pi, np.pi, m).astype(np.float32)
+    mass = rng.lognormal(np.log(8), 0.5, m).astype(np.float32)
+    om, idx, gap = orc.trijet_closest_mass(pt, eta, phi, mass, off, target=172.0)
+    for e, best in enumerate(_closest_brute(pt, eta, phi, mass, off, 172.0)):
+        if best is None:
+            assert np.isnan(om[e]) and (idx[e] == -1).all()
+            continue
+        _, mb, c = best
+        if gap[e] > 1e-6:   # the two FP64 formulas agree far below this
+            assert tuple(idx[e]) == c, (e, idx[e], c)
+        assert abs(om[e] - mb) <= 1e-9 * mb
+
+
+def test_trijet_closest_mass_closed_form_and_tie(orc):
+    # three massless objects at eta = 0, 120 degrees apart, pt = 172/3 each:
+    # no net momentum, E = 172, so their mass is 172; a fourth, harder object
+    # makes every other triplet heavier; the fifth repeats the third, so
+    # (0, 1, 2) and (0, 1, 4) tie exactly: the first wins
+    p = 172.0 / 3.0
+    pt = np.array([p, p, p, 400.0, p], np.float32)
+    eta = np.zeros(5, np.float32)
+    phi = np.array([0.0, 2 * np.pi / 3, -2 * np.pi / 3, 0.3, -2 * np.pi / 3], np.float32)
+    mass = np.zeros(5, np.float32)
+    off = np.array([0, 5, 7], np.int64)
+    pt2 = np.concatenate([pt, [50.0, 60.0]]).astype(np.float32)
+    eta2 = np.concatenate([eta, [0.1, 0.2]]).astype(np.float32)
+    phi2 = np.concatenate([phi, [0.1, 0.2]]).astype(np.float32)
+    mass2 = np.concatenate([mass, [1.0, 1.0]]).astype(np.float32)
+    om, idx, gap = orc.trijet_closest_mass(pt2, eta2, phi2, mass2, off, target=172.0)
+    assert tuple(idx[0]) == (0, 1, 2)
+    assert abs(om[0] - 172.0) < 1e-3   # float32 inputs: the triangle closes to ~1e-5 relative
+    assert gap[0] == 0.0
+    assert np.isnan(om[1]) and (idx[1] == -1).all() and np.isinf(gap[1])
+
+
+def _first_opposite_pair(q, on):
+    for i, j in itertools.combinations([k for k in range(len(q)) if on[k]], 2):
+        if q[i] * q[j] < 0:
+            return i, j
+    return None
+
+
+def test_select_opposite_sign_hand_cases(orc):
+    events = [[1, 1, -1], [1, 1], [-1, 1, 1, -1], [], [0, 1, -1], [1], [1, -1], [0, 0, 1]]
+    q = np.array([c for ev in events for c in ev], np.int8)
+    off = np.concatenate([[0], np.cumsum([len(ev) for ev in events])]).astype(np.int64)
+    out = orc.select_opposite_sign(q, off)
+    want = [[1, 0, 1], [0, 0], [1, 1, 0, 0], [], [0, 1, 1], [0], [1, 1], [0, 0, 0]]
+    np.testing.assert_array_equal(out, np.array([c for ev in want for c in ev], np.uint8))
+    # masked-in objects only; rows with mask_rows unset keep their values
+    mask_in = np.ones(len(q), np.uint8)
+    mask_in[off[2]] = 0                   # event 2 without its first muon: (1, 3) is the first pair
+    rows = np.ones(len(events), np.uint8)
+    rows[0] = 0
+    out = np.full(len(q), 7, np.uint8)
+    orc.select_opposite_sign(q, off, mask_rows=rows, mask_in=mask_in, out=out)
+    np.testing.assert_array_equal(out[off[0]:off[1]], [7, 7, 7])
+    np.testing.assert_array_equal(out[off[2]:off[3]], [0, 1, 0, 1])
+
+
+def test_select_opposite_sign_brute_force(orc):
+    rng = np.random.default_rng(41)
+    n = 2000
+    _, off = _jagged(rng, n, 2.5)
+    m = int(off[-1])
+    q = rng.choice(np.array([-1, 0, 1], np.int8), m, p=[0.45, 0.1, 0.45])
+    mask_in = (rng.random(m) < 0.8).astype(np.uint8)
+    out = orc.select_opposite_sign(q, off, mask_in=mask_in)
+    for e in range(n):
+        a, b = int(off[e]), int(off[e + 1])
+        want = np.zeros(b - a, np.uint8)
+        pair = _first_opposite_pair([int(x) for x in q[a:b]], mask_in[a:b])
+        if pair:
+            want[list(pair)] = 1
+        np.testing.assert_array_equal(out[a:b], want)
+
+
+def test_get_bin_contents_step_matches_numpy(orc):
+    rng = np.random.default_rng(51)
+    edges = np.sort(rng.uniform(-5, 5, 41)).astype(np.float32)     # uneven bins
+    contents = rng.normal(size=42).astype(np.float32)
+    x = np.concatenate([rng.uniform(-6, 6, 5000), edges, [np.nan, np.inf, -np.inf]]).astype(np.float32)
+    out = orc.get_bin_contents(x, edges, contents)
+    b = np.searchsorted(edges.astype(np.float64), x.astype(np.float64), side="right")
+    ok = ~np.isnan(x)
+    np.testing.assert_array_equal(out[ok], contents[b[ok]])
+    assert np.isnan(out[~ok]).all()
+
+
+def test_get_bin_contents_interpolation(orc):
+    rng = np.random.default_rng(52)
+    edges = np.linspace(0, 10, 11).astype(np.float32)
+    centres = ((edges[:-1] + edges[1:]) * np.float32(0.5)).astype(np.float32)
+    y = rng.normal(size=10).astype(np.float32)
+    contents = np.concatenate([[99.0], y, [-99.0]]).astype(np.float32)
+    # exact at the bin centres, clamped outside the first and last centre
+    np.testing.assert_array_equal(orc.get_bin_contents(centres, edges, contents, interpolate=True), y)
+    out = orc.get_bin_contents(np.array([-3, 0.2, 9.7, 40], np.float32), edges, contents, interpolate=True)
+    np.testing.assert_array_equal(out, [y[0], y[0], y[-1], y[-1]])
+    # between two centres the value lies between their contents
+    v = rng.uniform(0.5, 9.5, 4000).astype(np.float32)
+    out = orc.get_bin_contents(v, edges, contents, interpolate=True)
+    b = np.clip(np.floor(v.astype(np.float64) - 0.5).astype(int), 0, 8)
+    lo, hi = np.minimum(y[b], y[b + 1]), np.maximum(y[b], y[b + 1])
+    assert ((out >= lo - 1e-6) & (out <= hi + 1e-6)).all()
+    # contents linear in the centre are reproduced up to binary32 rounding
+    lin = np.concatenate([[0.0], 2.0 + 0.5 * centres, [0.0]]).astype(np.float32)
+    np.testing.assert_allclose(orc.get_bin_contents(v, edges, lin, interpolate=True),
+                               2.0 + 0.5 * v.astype(np.float64), rtol=1e-6, atol=1e-6)
+    # one bin: its content everywhere
+    one = orc.get_bin_contents(np.array([-1, 0.5, 3], np.float32), np.array([0, 1], np.float32),
+                               np.array([5, 6, 7], np.float32), interpolate=True)
+    np.testing.assert_array_equal(one, [6, 6, 6])
