@@ -221,6 +221,45 @@ hepacc_status hepacc_max_pt_trijet(const void *pt, const void *eta, const void *
                                    float *out_mass, float *out_pt, int32_t *out_idx3,
                                    hepacc_stream stream);
 
+/* Top-quark candidate (Section IV: the jet triplet with invariant mass
+ * closest to the top mass). For every event i with mask_rows[i] set: among
+ * triplets a<b<c of masked-in objects, the one whose mass (binary32,
+ * cancellation-free as in hepacc_pair_mass) is closest to target (first in
+ * lexicographic order on ties); out_mass[i] its mass, out_idx3[3i..3i+2]
+ * its local indices. Fewer than three objects: NaN and -1 -1 -1. Either
+ * output may be NULL (not both). */
+hepacc_status hepacc_trijet_closest_mass(const void *pt, const void *eta, const void *phi, const void *mass,
+                                         hepacc_dtype type, const void *offsets, hepacc_dtype offsets_type,
+                                         int64_t n_rows, const uint8_t *mask_rows, const uint8_t *mask_content,
+                                         float target, float *out_mass, int32_t *out_idx3, hepacc_stream stream);
+
+/* select_opposite_sign_muons (Section III, specialised kernels). For every
+ * event i with mask_rows[i] set: over the objects with mask_in set, in
+ * stored order (the pt order of the data), the first object that has a
+ * later one of opposite charge (charge_a * charge_b < 0), and the first such
+ * partner; mask_out is 1 for those two and 0 for every other object of the
+ * event (all 0 without such a pair). Objects of events with mask_rows unset
+ * are untouched. charge is int8 (content size); mask_in may be NULL (all
+ * objects); mask_out must not alias mask_in. */
+hepacc_status hepacc_select_opposite_sign(const int8_t *charge, const void *offsets, hepacc_dtype offsets_type,
+                                          int64_t n_rows, const uint8_t *mask_rows, const uint8_t *mask_in,
+                                          uint8_t *mask_out, hepacc_stream stream);
+
+/* get_bin_contents (Section III: lookup histograms for reweighting). For
+ * j < n: with interpolate = 0, out[j] = contents[b] for the bin b of
+ * data[j] as in hepacc_fill_histogram (contents has nbins+2 entries,
+ * under- and overflow included); with interpolate != 0, the linear
+ * interpolation between the contents of neighbouring in-range bins at
+ * their centres c_b = (edges[b-1] + edges[b]) * 0.5, clamped to
+ * contents[1] below c_1 and contents[nbins] at or above c_nbins:
+ * t = (v - c_b) / (c_b+1 - c_b), out = contents[b] + t * (contents[b+1] -
+ * contents[b]) for c_b <= v < c_b+1, every operation in binary32 rounded as
+ * written. NaN data gives NaN. edges (nbins+1, increasing) and contents are
+ * DEVICE float32; 1 <= nbins <= 65536; data_type F32, F16 or BF16. */
+hepacc_status hepacc_get_bin_contents(const void *data, hepacc_dtype data_type, int64_t n, const float *edges,
+                                      int32_t nbins, const float *contents, int32_t interpolate, float *out,
+                                      hepacc_stream stream);
+
 /* ---------------------------------------------------------------------------
  * The fused analysis chain (Section IV benchmark analysis), one launch
  * ------------------------------------------------------------------------- */

@@ -270,6 +270,157 @@ __global__ void __launch_bounds__(kBlock) k_pair_mass(const T* pt, const T* eta,
     }
 }
 
+// Top candidate (Section IV): the triplet of masked-in objects whose mass
+// is closest to the target, lane = event. The objects' mass terms are
+// prepared once per event (up to kCloseLocal of them; beyond that they are
+// recomputed per triplet); ties keep the first triplet in lexicographic order.
+constexpr int kCloseLocal = 12;
+
+template <typename T, typename OffT>
+__global__ void __launch_bounds__(kBlock) k_trijet_closest(const T* pt, const T* eta, const T* phi, const T* mass,
+                                                           const OffT* off, int64_t n, const uint8_t* mask_rows,
+                                                           const uint8_t* mask_content, float target,
+                                                           float* out_mass, int32_t* out_idx3) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask_rows && !mask_rows[e]) continue;
+        const int64_t i0 = ldoff(off, e), i1 = ldoff(off, e + 1);
+        auto on = [&](int64_t i) { return mask_content == nullptr || mask_content[i] != 0; };
+        auto obj = [&](int64_t i) { return mass_obj(ldf(pt, i), ldf(eta, i), ldf(phi, i), ldf(mass, i)); };
+        MassObj o[kCloseLocal];
+        int32_t li[kCloseLocal];
+        int cnt = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            if (!on(i)) continue;
+            if (cnt < kCloseLocal) {
+                o[cnt] = obj(i);
+                li[cnt] = static_cast<int32_t>(i - i0);
+            }
+            ++cnt;
+        }
+        float best_d = INFINITY, best_m = __int_as_float(0x7fc00000);
+        int32_t ba = -1, bb = -1, bc = -1;
+        if (cnt >= 3 && cnt <= kCloseLocal) {
+            for (int a = 0; a < cnt; ++a)
+                for (int b = a + 1; b < cnt; ++b)
+                    for (int c = b + 1; c < cnt; ++c) {
+                        const float m = mass3obj(o[a], o[b], o[c]);
+                        const float d = fabsf(m - target);
+                        if (d < best_d) {
+                            best_d = d;
+                            best_m = m;
+                            ba = li[a];
+                            bb = li[b];
+                            bc = li[c];
+                        }
+                    }
+        } else if (cnt > kCloseLocal) {
+            for (int64_t a = i0; a < i1; ++a) {
+                if (!on(a)) continue;
+                const MassObj oa = obj(a);
+                for (int64_t b = a + 1; b < i1; ++b) {
+                    if (!on(b)) continue;
+                    const MassObj ob = obj(b);
+                    for (int64_t c = b + 1; c < i1; ++c) {
+                        if (!on(c)) continue;
+                        const float m = mass3obj(oa, ob, obj(c));
+                        const float d = fabsf(m - target);
+                        if (d < best_d) {
+                            best_d = d;
+                            best_m = m;
+                            ba = static_cast<int32_t>(a - i0);
+                            bb = static_cast<int32_t>(b - i0);
+                            bc = static_cast<int32_t>(c - i0);
+                        }
+                    }
+                }
+            }
+        }
+        if (out_mass) out_mass[e] = best_m;
+        if (out_idx3) {
+            out_idx3[3 * e] = ba;
+            out_idx3[3 * e + 1] = bb;
+            out_idx3[3 * e + 2] = bc;
+        }
+    }
+}
+
+// select_opposite_sign_muons (Section III), lane = event: over masked-in
+// objects in stored order, the first i with a later masked-in j of opposite
+// charge, and the first such j; those two are kept, every other object of
+// the event is masked out.
+template <typename OffT>
+__global__ void __launch_bounds__(kBlock) k_opposite_sign(const int8_t* charge, const OffT* off, int64_t n,
+                                                          const uint8_t* mask_rows, const uint8_t* mask_in,
+                                                          uint8_t* mask_out) {
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask_rows && !mask_rows[e]) continue;
+        const int64_t i0 = ldoff(off, e), i1 = ldoff(off, e + 1);
+        auto on = [&](int64_t i) { return mask_in == nullptr || mask_in[i] != 0; };
+        int64_t a = -1, b = -1;
+        for (int64_t i = i0; i < i1 && a < 0; ++i) {
+            if (!on(i)) continue;
+            const int qi = charge[i];
+            for (int64_t j = i + 1; j < i1; ++j) {
+                if (on(j) && qi * static_cast<int>(charge[j]) < 0) {
+                    a = i;
+                    b = j;
+                    break;
+                }
+            }
+        }
+        for (int64_t i = i0; i < i1; ++i) mask_out[i] = (i == a || i == b) ? 1 : 0;
+    }
+}
+
+// get_bin_contents (Section III), lane = element: the content of the value's
+// bin, or the binary32 linear interpolation between the contents of the two
+// neighbouring in-range bin centres c_b = (e[b-1] + e[b]) * 0.5 (clamped to
+// the first and last centre), every operation rounded as written.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bin_contents(const T* x, int64_t n, const float* __restrict__ edges,
+                                                         int nb, const float* __restrict__ contents,
+                                                         int interpolate, float* out) {
+    const float e0 = __ldg(edges), en = __ldg(edges + nb);
+    const float span = en - e0;
+    const float invw = span > 0.0f ? static_cast<float>(nb) / span : 0.0f;
+    auto centre = [&](int b) { return __fmul_rn(__fadd_rn(__ldg(edges + b - 1), __ldg(edges + b)), 0.5f); };
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float v = ldf(x, j);
+        if (v != v) {
+            out[j] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        if (!interpolate) {
+            out[j] = __ldg(contents + find_bin(v, edges, nb, invw));
+            continue;
+        }
+        if (nb == 1 || v < centre(1)) {
+            out[j] = __ldg(contents + 1);
+            continue;
+        }
+        if (v >= centre(nb)) {
+            out[j] = __ldg(contents + nb);
+            continue;
+        }
+        // the smallest b in [1, nb-1] with v < c_{b+1} (then c_b <= v)
+        int lo = 1, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (v < centre(mid + 1))
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const float cb = centre(lo), cb1 = centre(lo + 1);
+        const float yb = __ldg(contents + lo), yb1 = __ldg(contents + lo + 1);
+        const float t = __fdiv_rn(__fsub_rn(v, cb), __fsub_rn(cb1, cb));
+        out[j] = __fadd_rn(yb, __fmul_rn(t, __fsub_rn(yb1, yb)));
+    }
+}
+
 template <typename T, typename OffT>
 __global__ void __launch_bounds__(kBlock) k_set(T* x, const OffT* off, int64_t n, const int32_t* nth, int32_t nth_scalar,
                                                 const uint8_t* mask_rows, const uint8_t* mask_content, T value) {
@@ -761,6 +912,61 @@ hepacc_status hepacc_max_pt_trijet(const void* pt, const void* eta, const void* 
             return launch_tiles(k_trijet<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows, out_mass,
                                 out_pt, out_idx3);
         });
+    });
+}
+
+hepacc_status hepacc_trijet_closest_mass(const void* pt, const void* eta, const void* phi, const void* mass,
+                                         hepacc_dtype t, const void* offsets, hepacc_dtype ot, int64_t n,
+                                         const uint8_t* mask_rows, const uint8_t* mask_content, float target,
+                                         float* out_mass, int32_t* out_idx3, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(pt && eta && phi && mass && offsets, "missing required pointer");
+    HEPACC_CHECK(out_mass || out_idx3, "no output requested");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        return with_float_type(t, [&](auto tt) -> hepacc_status {
+            using T = typename decltype(tt)::type;
+            k_trijet_closest<T, O><<<flat_grid(n), kBlock, 0, s>>>(
+                static_cast<const T*>(pt), static_cast<const T*>(eta), static_cast<const T*>(phi),
+                static_cast<const T*>(mass), static_cast<const O*>(offsets), n, mask_rows, mask_content, target,
+                out_mass, out_idx3);
+            HEPACC_CHECK_LAUNCH("trijet_closest_mass launch");
+            return HEPACC_OK;
+        });
+    });
+}
+
+hepacc_status hepacc_select_opposite_sign(const int8_t* charge, const void* offsets, hepacc_dtype ot, int64_t n,
+                                          const uint8_t* mask_rows, const uint8_t* mask_in, uint8_t* mask_out,
+                                          hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n_rows < 0");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(charge && offsets && mask_out, "charge, offsets and mask_out are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        k_opposite_sign<O><<<flat_grid(n), kBlock, 0, s>>>(charge, static_cast<const O*>(offsets), n, mask_rows,
+                                                            mask_in, mask_out);
+        HEPACC_CHECK_LAUNCH("select_opposite_sign launch");
+        return HEPACC_OK;
+    });
+}
+
+hepacc_status hepacc_get_bin_contents(const void* data, hepacc_dtype dt, int64_t n, const float* edges, int32_t nbins,
+                                      const float* contents, int32_t interpolate, float* out, hepacc_stream stream) {
+    HEPACC_CHECK(n >= 0, "n < 0");
+    HEPACC_CHECK(nbins >= 1 && nbins <= 65536, "nbins must be in [1, 65536]");
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(data && edges && contents && out, "data, edges, contents and out are required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return with_float_type(dt, [&](auto tt) -> hepacc_status {
+        using T = typename decltype(tt)::type;
+        k_bin_contents<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(data), n, edges, nbins, contents,
+                                                          interpolate ? 1 : 0, out);
+        HEPACC_CHECK_LAUNCH("get_bin_contents launch");
+        return HEPACC_OK;
     });
 }
 

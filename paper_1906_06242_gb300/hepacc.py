@@ -65,7 +65,8 @@ def load(build_if_missing: bool = True):
                  "hepacc_mask_deltar", "hepacc_fill_histogram", "hepacc_pair_mass", "hepacc_max_pt_trijet",
                  "hepacc_run_chain", "hepacc_validate_offsets", "hepacc_device_error",
                  "hepacc_selftest_wait_timeout", "hepacc_plan_create", "hepacc_plan_run",
-                 "hepacc_plan_describe"):
+                 "hepacc_plan_describe", "hepacc_trijet_closest_mass", "hepacc_select_opposite_sign",
+                 "hepacc_get_bin_contents"):
         getattr(L, name).restype = ctypes.c_int
     L.hepacc_plan_destroy.restype = None
     L.hepacc_plan_destroy.argtypes = [ctypes.c_void_p]
@@ -263,6 +264,42 @@ def hepacc_max_pt_trijet(pt, eta, phi, mass, offsets, mask_rows=None, mask_conte
                                        _code(offsets), _i64(n), _ptr(mask_rows), _ptr(mask_content),
                                        _ptr(out_mass), _ptr(out_pt), _ptr(out_idx3), _stream(stream)))
     return out_mass, out_pt, out_idx3
+
+
+def hepacc_trijet_closest_mass(pt, eta, phi, mass, offsets, target=172.0, mask_rows=None, mask_content=None,
+                               out_mass=None, out_idx3=None, stream=None):
+    """Top candidate: the triplet of masked-in objects with mass closest to
+    ``target``; returns (mass [N] float32, idx3 [N,3] int32)."""
+    n = offsets.numel() - 1
+    if out_mass is None:
+        out_mass = torch.full((n,), float("nan"), dtype=torch.float32, device=pt.device)
+    if out_idx3 is None:
+        out_idx3 = torch.full((n, 3), -7, dtype=torch.int32, device=pt.device)
+    _check(load().hepacc_trijet_closest_mass(_ptr(pt), _ptr(eta), _ptr(phi), _ptr(mass), _code(pt), _ptr(offsets),
+                                             _code(offsets), _i64(n), _ptr(mask_rows), _ptr(mask_content),
+                                             _f32(target), _ptr(out_mass), _ptr(out_idx3), _stream(stream)))
+    return out_mass, out_idx3
+
+
+def hepacc_select_opposite_sign(charge, offsets, mask_rows=None, mask_in=None, mask_out=None, stream=None):
+    """Keep the first two masked-in objects of opposite charge per event."""
+    n = offsets.numel() - 1
+    if mask_out is None:
+        mask_out = torch.zeros(charge.numel(), dtype=torch.uint8, device=charge.device)
+    _check(load().hepacc_select_opposite_sign(_ptr(charge), _ptr(offsets), _code(offsets), _i64(n),
+                                              _ptr(mask_rows), _ptr(mask_in), _ptr(mask_out), _stream(stream)))
+    return mask_out
+
+
+def hepacc_get_bin_contents(data, edges, contents, interpolate=False, out=None, stream=None):
+    """Histogram lookup (bin contents, or binary32 linear interpolation
+    between bin centres); edges and contents are float32 device tensors."""
+    if out is None:
+        out = torch.empty(data.numel(), dtype=torch.float32, device=data.device)
+    _check(load().hepacc_get_bin_contents(_ptr(data), _code(data), _i64(data.numel()), _ptr(edges),
+                                          _i32(edges.numel() - 1), _ptr(contents), _i32(1 if interpolate else 0),
+                                          _ptr(out), _stream(stream)))
+    return out
 
 
 def hepacc_validate_offsets(offsets, content_len, first_bad=None, stream=None):
