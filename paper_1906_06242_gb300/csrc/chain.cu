@@ -164,7 +164,7 @@ bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_
     L.stage_bytes = up(kHdr + off);
     size_t at = 0;
     region(at, 2 * static_cast<size_t>(L.stage_bytes));
-    L.bars = region(at, 32 + 48 + 16);   // four mbarriers, spans of the next tile
+    L.bars = region(at, 32 + 48 + 48 + 16);   // four mbarriers, spans of two tiles
     L.edges = region(at, static_cast<size_t>((P.n_edges + 3) & ~3) * 4);
     L.queue = region(at, static_cast<size_t>(E) * R_WORDS * 4);
     L.acc_words = static_cast<int>(cj / 32 + 2);

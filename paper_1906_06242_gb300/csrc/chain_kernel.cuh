@@ -5,8 +5,9 @@
 //
 // One kernel, persistent blocks; a block works on tiles of E = blockDim.x
 // consecutive events (thread = event):
-//  * staging: thread 0 copies every needed column's span of the tile into
-//    one of two shared-memory stage buffers with bulk asynchronous copies
+//  * staging: warp 0 copies every needed column's span of the tile (one
+//    lane per column) into one of two shared-memory stage buffers with bulk
+//    asynchronous copies
 //    (cp.async.bulk, the TMA engine; whole 16-byte chunks), completion on a
 //    "full" mbarrier; warps release a stage on an "empty" mbarrier, so they
 //    run independently (up to one tile apart) without block barriers; the
@@ -280,60 +281,60 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
         }
     };
 
-    // thread 0: first and last element of every collection in tile tt
-    auto load_span = [&](int64_t tt, int64_t (&S)[3], int64_t (&T)[3]) {
-        int ts;
-        int64_t lt;
-        where(tt, ts, lt);
-        const int64_t ns = SDs(ts).n;
-        const int64_t a = lt * E;
-        const int64_t z = a + E < ns ? a + E : ns;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            S[c] = ldoff(static_cast<const OffT*>(SDs(ts).off[c]), a);
-            T[c] = ldoff(static_cast<const OffT*>(SDs(ts).off[c]), z);
+    // Warp 0 stages the tiles. load_span: the first and last element of
+    // every collection in tile tt, span[0..2] and span[3..5] (shared
+    // memory), one lane each.
+    auto load_span = [&](int64_t tt, int64_t* span) {
+        __syncwarp();   // earlier readers of span are done
+        if (lane < 6) {
+            int ts;
+            int64_t lt;
+            where(tt, ts, lt);
+            const int64_t ns = SDs(ts).n;
+            const int64_t a = lt * E;
+            const int64_t z = a + E < ns ? a + E : ns;
+            span[lane] = ldoff(static_cast<const OffT*>(SDs(ts).off[lane % 3]), lane < 3 ? a : z);
         }
+        __syncwarp();
     };
-    // thread 0: header of stage b and the bulk copies of the spans of tile
-    // tt (sample ts)
-    auto issue = [&](int b, int ts, const int64_t (&S)[3], const int64_t (&T)[3]) {
+    // issue: header of stage b and the bulk copies of the spans of tile tt
+    // (sample ts), column c by lane c; the copies are issued after lane 0
+    // registered their total on the stage's "full" mbarrier
+    auto issue = [&](int b, int ts, const int64_t* span) {
         const SampleDesc& sd = SDs(ts);
         unsigned char* st = smem + b * L.stage_bytes;
         int64_t* hdr = reinterpret_cast<int64_t*>(st);
         uint32_t* hoff = reinterpret_cast<uint32_t*>(st + 32);
-        bool fits = true;
-        uint32_t total = 0;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const ColSpec& cs = L.col[c];
-            const uintptr_t cb = reinterpret_cast<uintptr_t>(sd.col[c]);
-            const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
-            const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
-            const uintptr_t bytes = T[cs.coll] > S[cs.coll] ? ((z + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)) : 0;
-            if (bytes > cs.cap) fits = false;
-            total += static_cast<uint32_t>(bytes);
-            hoff[c] = b * L.stage_bytes + kHdr + cs.soff + static_cast<uint32_t>(a & 15u);
+        uint32_t bytes = 0;
+        uintptr_t a16 = 0;
+        bool fits_c = true;
+        if (lane < NC) {
+            const ColSpec& cs = L.col[lane];
+            const int64_t S = span[cs.coll], T = span[3 + cs.coll];
+            const uintptr_t cb = reinterpret_cast<uintptr_t>(sd.col[lane]);
+            const uintptr_t a = cb + static_cast<uintptr_t>(S) * cs.es;
+            const uintptr_t z = cb + static_cast<uintptr_t>(T) * cs.es;
+            a16 = a & ~uintptr_t(15);
+            bytes = T > S ? static_cast<uint32_t>(((z + 15) & ~uintptr_t(15)) - a16) : 0u;
+            fits_c = bytes <= cs.cap;
+            hoff[lane] = b * L.stage_bytes + kHdr + cs.soff + static_cast<uint32_t>(a & 15u);
         }
-        hdr[0] = S[0];
-        hdr[1] = S[1];
-        hdr[2] = S[2];
-        hoff[NC] = fits ? 1u : 0u;
-        fence_proxy_async_smem();
-        if (fits) {
-            mbar_arrive_expect_tx(full[b], total);
+        const bool fits = __all_sync(0xffffffffu, fits_c);
+        uint32_t total = bytes;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const ColSpec& cs = L.col[c];
-                if (T[cs.coll] <= S[cs.coll]) continue;
-                const uintptr_t cb = reinterpret_cast<uintptr_t>(sd.col[c]);
-                const uintptr_t a = cb + static_cast<uintptr_t>(S[cs.coll]) * cs.es;
-                const uintptr_t z = cb + static_cast<uintptr_t>(T[cs.coll]) * cs.es;
-                const uintptr_t a16 = a & ~uintptr_t(15);
-                const uint32_t bytes = static_cast<uint32_t>(((z + 15) & ~uintptr_t(15)) - a16);
-                bulk_g2s(smem0 + b * L.stage_bytes + kHdr + cs.soff, reinterpret_cast<const void*>(a16), bytes, full[b]);
-            }
-        } else {
-            mbar_arrive_expect_tx(full[b], 0);
+        for (int d = 16; d >= 1; d >>= 1) total += __shfl_xor_sync(0xffffffffu, total, d);
+        if (lane < 3) hdr[lane] = span[lane];
+        if (lane == 0) hoff[NC] = fits ? 1u : 0u;
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(full[b], fits ? total : 0u);
+        }
+        __syncwarp();
+        if (fits && lane < NC && bytes > 0) {
+            fence_proxy_async_smem();
+            bulk_g2s(smem0 + b * L.stage_bytes + kHdr + L.col[lane].soff, reinterpret_cast<const void*>(a16), bytes,
+                     full[b]);
         }
     };
 
@@ -481,10 +482,10 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
     };
 
     int qcount = 0;
-    int64_t (&S1)[3] = *reinterpret_cast<int64_t(*)[3]>(smem + L.bars + 32);   // thread 0: spans of the next tile
-    int64_t (&T1)[3] = *reinterpret_cast<int64_t(*)[3]>(smem + L.bars + 56);
+    int64_t* span1 = reinterpret_cast<int64_t*>(smem + L.bars + 32);   // warp 0: spans of the tile after next
+    int64_t* span0 = reinterpret_cast<int64_t*>(smem + L.bars + 80);   // warp 0: spans of a sample's first tile
     uint32_t fpar[2] = {0u, 0u};
-    uint32_t uses[2] = {0u, 0u};   // thread 0: copies issued into each stage
+    uint32_t uses[2] = {0u, 0u};   // warp 0: copies issued into each stage
     int b = 0;
     bool stop = false;   // a bounded wait gave up: skip the remaining work, keep the barriers
     // this thread's offsets and weight of tile t (loaded a tile ahead)
@@ -520,36 +521,35 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
     int64_t cs_[3] = {0, 0, 0}, ct_[3] = {0, 0, 0};
     float cw_ = 0.0f;   // this thread's event weight, loaded a tile ahead like its offsets
     if (tile < ntiles) {
-        if (tid == 0) {
-            int64_t S0[3], T0[3];
-            load_span(tile, S0, T0);
+        if (warp == 0) {
+            load_span(tile, span0);
             // the stage is free once every warp released its last use
             bool ok = true;
             if (uses[b] > 0) ok = mbar_wait_bounded(empty[b], (uses[b] - 1) & 1u);
-            if (ok) {
+            if (__all_sync(0xffffffffu, ok)) {
                 int ts;
                 int64_t lt;
                 where(tile, ts, lt);
-                issue(b, ts, S0, T0);
+                issue(b, ts, span0);
                 ++uses[b];
             }
-            if (tile + grid < ntiles) load_span(tile + grid, S1, T1);
+            if (tile + grid < ntiles) load_span(tile + grid, span1);
         }
         own_offsets(tile, cs_, ct_, cw_);
     }
     for (; tile < ntiles; tile += grid) {
         const int64_t next = tile + grid;
-        if (tid == 0 && next < ntiles) {
+        if (warp == 0 && next < ntiles) {
             // the other stage is free once every warp released its previous tile
             bool ok = true;
             if (uses[b ^ 1] > 0) ok = mbar_wait_bounded(empty[b ^ 1], (uses[b ^ 1] - 1) & 1u);
-            if (ok) {
+            if (__all_sync(0xffffffffu, ok)) {
                 int ts;
                 int64_t lt;
                 where(next, ts, lt);
-                issue(b ^ 1, ts, S1, T1);
+                issue(b ^ 1, ts, span1);
                 ++uses[b ^ 1];
-                if (next + grid < ntiles) load_span(next + grid, S1, T1);
+                if (next + grid < ntiles) load_span(next + grid, span1);
             }
         }
         __syncwarp();
