@@ -179,8 +179,10 @@ __device__ __forceinline__ MassObj mass_obj(float pt, float eta, float phi, floa
     const float p = pt * 0.5f * (ex + emx);   // pt cosh(eta)
     o.e = sqrtf(p * p + m2);
     if (pt > 0.0f) {
+        // c = (log1p(u e^-eta) - log1p(u e^eta)) / 2 as one logarithm:
+        // log1p(-u (e^eta - e^-eta) / (1 + u e^eta)) / 2
         const float u = __fdividef(__fdividef(m2, o.e + p), pt);
-        o.c = 0.5f * (log1pf(u * emx) - log1pf(u * ex));
+        o.c = 0.5f * log1pf(-__fdividef(u * (ex - emx), 1.0f + u * ex));
     } else {
         o.c = 0.0f;
     }
