@@ -54,6 +54,8 @@ hepacc_status make_params(const hepacc_chain_config* cfg, ChainParams& P) {
         }
         const float span = cfg->edges[ne + nb] - cfg->edges[ne];
         P.invw[h] = span > 0.0f ? static_cast<float>(nb) / span : 0.0f;
+        P.e_lo[h] = cfg->edges[ne];
+        P.e_hi[h] = cfg->edges[ne + nb];
         ne += nb + 1;
         nbt += nb + 2;
     }

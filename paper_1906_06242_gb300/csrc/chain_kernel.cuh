@@ -74,6 +74,7 @@ struct ChainParams {
     int eoff[kNV];      // first edge of histogram h
     int boff[kNV];      // first bin of histogram h inside a variation block
     float invw[kNV];    // bins per unit of histogram h (first guess of the bin search)
+    float e_lo[kNV], e_hi[kNV];   // first and last edge of histogram h
     float edges[HEPACC_CHAIN_MAX_EDGES];
 };
 
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
                 var[17] = __fadd_rn(var[0], var[13]);
             }
             MassObj ol, os;
+            float p_ls = 0.0f;   // E_lead E_sub - p_lead . p_sub, shared with the triplet
             if (lead >= 0) {
                 var[1] = f(R_J1);
                 var[2] = f(R_J1 + 1);
@@ -382,7 +384,8 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
             if (sub >= 0) {
                 var[6] = f(R_J2);
                 os = mass_obj(var[6], f(R_J2 + 1), f(R_J2 + 2), f(R_J2 + 3));
-                var[7] = mass2obj(ol, os);
+                p_ls = pair_dot(ol, os);
+                var[7] = sqrtf(ol.m * ol.m + os.m * os.m + 2.0f * p_ls);
             }
             if (njet >= 3) {
                 // the triplet's four-momenta; jets shared with the leading pair reuse its terms
@@ -392,7 +395,12 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
                     return mass_obj(f(w), f(w + 1), f(w + 2), f(w + 3));
                 };
                 const MassObj oa = obj(ta, R_T1), ob = obj(tb, R_T2), oc = obj(tc, R_T3);
-                var[11] = mass3obj(oa, ob, oc);
+                auto pd = [&](int i, const MassObj& x, int j, const MassObj& y) {
+                    if ((i == lead && j == sub) || (i == sub && j == lead)) return p_ls;
+                    return pair_dot(x, y);
+                };
+                const float msum = oa.m * oa.m + ob.m * ob.m + oc.m * oc.m;
+                var[11] = sqrtf(msum + 2.0f * (pd(ta, oa, tb, ob) + pd(ta, oa, tc, oc) + pd(tb, ob, tc, oc)));
                 var[12] = sqrtf(f(R_BEST));
             }
             if (DEBUG) {
@@ -437,7 +445,7 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
                     for (int h = 0; h < kNV; ++h) {
                         const float* eh = s_edges + P.eoff[h];
                         const int nb_h = P.nbins[h];
-                        const int bin = find_bin(__uint_as_float(q[h]), eh, nb_h, P.invw[h]);
+                        const int bin = find_bin_lim(__uint_as_float(q[h]), eh, P.e_lo[h], P.e_hi[h], nb_h, P.invw[h]);
                         if (bin < 0) continue;
                         const int at = static_cast<int>(kk) * P.total_bins + P.boff[h] + bin;
                         atomicAdd(&out.counts[at], 1ull);

@@ -171,11 +171,12 @@ __device__ __forceinline__ MassObj mass_obj(float pt, float eta, float phi, floa
     o.m = m;
     const float m2 = m * m;
     o.mt = sqrtf(pt * pt + m2);
-    // e^eta to a few 1e-7 relative (the approximate exponential): it enters
-    // the energy and the small rapidity correction c only, never a
-    // difference that cancels
+    // e^eta and e^-eta to a few 1e-7 relative (the approximate exponential):
+    // they enter the energy and the small rapidity correction c only; their
+    // difference in c loses relative accuracy near eta = 0, where c (of
+    // order u eta) is negligible against the rapidity difference it corrects
     const float ex = __expf(eta);
-    const float emx = __frcp_rn(ex);
+    const float emx = __expf(-eta);
     const float p = pt * 0.5f * (ex + emx);   // pt cosh(eta)
     o.e = sqrtf(p * p + m2);
     if (pt > 0.0f) {
@@ -218,6 +219,18 @@ __device__ __forceinline__ float mass3obj(const MassObj& a, const MassObj& b, co
 // The first guess assumes uniform spacing; the explicit comparisons that
 // follow make the result exact for any increasing edges.
 // ---------------------------------------------------------------------------
+
+// The same with the first and last edge given (e0 = e[0], en = e[nb]).
+__device__ __forceinline__ int find_bin_lim(float v, const float* e, float e0, float en, int nb, float inv_width) {
+    if (v != v) return -1;
+    if (v < e0) return 0;
+    if (v >= en) return nb + 1;
+    int b = static_cast<int>((v - e0) * inv_width) + 1;
+    b = b < 1 ? 1 : (b > nb ? nb : b);
+    while (b > 1 && v < e[b - 1]) --b;
+    while (b < nb && v >= e[b]) ++b;
+    return b;
+}
 
 __device__ __forceinline__ int find_bin(float v, const float* e, int nb, float inv_width) {
     if (v != v) return -1;
