@@ -361,9 +361,12 @@ typedef struct hepacc_plan hepacc_plan;
 #define HEPACC_PLAN_HIST_GLOBAL 32      /* global memory */
 
 /* Builds a plan that runs the chain of hepacc_run_chain over samples[0..n)
- * with one configuration, sixteen samples per persistent launch: every block
- * walks through the samples in turn, so blocks idle on a small sample move
- * to the next. Sample i adds to outputs[i] (counts, sumw, sumw2 as in
+ * with one configuration, up to sixteen samples per persistent launch. With
+ * global histograms the samples' tiles form one range that the blocks share
+ * (no block waits at a sample boundary); with shared-memory histograms
+ * every block walks through the samples in turn and adds its histograms to
+ * a sample's outputs when done with it. Sample i adds to outputs[i]
+ * (counts, sumw, sumw2 as in
  * hepacc_run_chain; per-event arrays must be NULL). All samples use I64
  * offsets and the same kin_type and btag_type (F32 with F32, F16 with F16
  * or BF16). Histogram placement is a kernel configuration: block-private

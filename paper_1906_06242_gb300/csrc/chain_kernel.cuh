@@ -45,7 +45,6 @@ namespace chain {
 
 constexpr int NC = 15;            // staged columns
 constexpr int kNV = HEPACC_CHAIN_NVARS;
-constexpr int kQ = kNV + 1;       // fill entry: 20 variables + variation
 constexpr int kScratch = 10;      // selected jets ranked from a queue slot (2 x 10 words of it)
 // Block shape of each launch form: threads per block (the largest tile) and
 // blocks per SM, measured best on GB300. Register allocation rounds blocks
@@ -167,10 +166,6 @@ enum : int {
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
-template <typename T>
-__device__ __forceinline__ float gload(const void* p, int64_t i) {
-    return Elem<T>::f(static_cast<const T*>(p)[i]);
-}
 
 // Column access for the selection phase.
 struct StagedCols {
