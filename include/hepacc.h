@@ -339,7 +339,11 @@ typedef struct {
  *     iso, ST = HT + lepton pt, sum of selected-jet masses, event weight;
  *  5. every passing event adds its weight to one bin of each histogram
  *     (the trijet ones only when n_jet >= 3).
- * One kernel launch; each input column is read once. */
+ * One kernel launch; each input column is read once.
+ * Debug checks: with the environment variable HEPACC_DEBUG set (and not 0)
+ * the three offsets arrays are first checked on the device (offsets[0] >= 0,
+ * non-decreasing; the call waits for the check); a failure returns
+ * HEPACC_ERR_DEVICE_CHECK before the chain is launched. */
 hepacc_status hepacc_run_chain(const hepacc_event_batch *batch, const hepacc_chain_config *config,
                                const hepacc_chain_outputs *out, hepacc_stream stream);
 
@@ -359,6 +363,7 @@ typedef struct hepacc_plan hepacc_plan;
 #define HEPACC_PLAN_HIST_CLUSTER8 8     /* shared memory of a cluster of 8 blocks */
 #define HEPACC_PLAN_HIST_CLUSTER16 16   /* shared memory of a cluster of 16 blocks */
 #define HEPACC_PLAN_HIST_GLOBAL 32      /* global memory */
+#define HEPACC_PLAN_VALIDATE 64         /* check every sample's offsets on the device at creation */
 
 /* Builds a plan that runs the chain of hepacc_run_chain over samples[0..n)
  * with one configuration, up to sixteen samples per persistent launch. With
@@ -378,8 +383,10 @@ typedef struct hepacc_plan hepacc_plan;
  * here must be valid), the fastest kept, and the outputs cleared to zero
  * afterwards, on `stream`, which the call synchronises. config is HOST
  * memory and copied; the sample and output structs are copied; the device
- * buffers they point to must stay valid for the plan's life. *plan is NULL
- * on error. */
+ * buffers they point to must stay valid for the plan's life. With
+ * HEPACC_PLAN_VALIDATE (or HEPACC_DEBUG set, as for hepacc_run_chain) every
+ * sample's offsets are checked first; a failure returns
+ * HEPACC_ERR_DEVICE_CHECK and nothing runs. *plan is NULL on error. */
 hepacc_status hepacc_plan_create(const hepacc_chain_config *config, int32_t n_samples,
                                  const hepacc_event_batch *samples, const hepacc_chain_outputs *outputs,
                                  int32_t flags, hepacc_stream stream, hepacc_plan **plan);

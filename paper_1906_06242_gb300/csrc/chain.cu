@@ -78,6 +78,16 @@ hepacc_status check_batch(const hepacc_event_batch* b) {
     return HEPACC_OK;
 }
 
+// The three offsets arrays of a batch checked on the device (debug checks).
+hepacc_status check_batch_offsets(const hepacc_event_batch* b, cudaStream_t s) {
+    const void* offs[3] = {b->jet_offsets, b->mu_offsets, b->el_offsets};
+    for (const void* o : offs) {
+        const hepacc_status st = check_offsets_nondecreasing(o, b->offsets_type, b->n_events, s);
+        if (st != HEPACC_OK) return st;
+    }
+    return HEPACC_OK;
+}
+
 bool has_per_event(const hepacc_chain_outputs* o) {
     return o->ev_pass || o->ev_nlep || o->ev_njet || o->ev_nb || o->ev_idx || o->ev_vars;
 }
@@ -220,6 +230,10 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     st = check_batch(b);
     if (st != HEPACC_OK) return st;
     if (b->n_events == 0) return HEPACC_OK;
+    if (debug_checks()) {
+        st = check_batch_offsets(b, reinterpret_cast<cudaStream_t>(stream));
+        if (st != HEPACC_OK) return st;
+    }
     BatchDesc B;
     std::memset(&B, 0, sizeof B);
     B.n_samples = 1;
@@ -391,7 +405,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     if (n_samples < 1 || !samples || !outputs) return fail(HEPACC_ERR_INVALID_ARG, "need at least one sample and its outputs");
     const int hist_flags = HEPACC_PLAN_HIST_BLOCK | HEPACC_PLAN_HIST_CLUSTER8 | HEPACC_PLAN_HIST_CLUSTER16 |
                            HEPACC_PLAN_HIST_GLOBAL;
-    if (flags & ~(HEPACC_PLAN_AUTOTUNE | HEPACC_PLAN_GRAPH | hist_flags))
+    if (flags & ~(HEPACC_PLAN_AUTOTUNE | HEPACC_PLAN_GRAPH | HEPACC_PLAN_VALIDATE | hist_flags))
         return fail(HEPACC_ERR_INVALID_ARG, "unknown plan flags");
     const int allowed = (flags & hist_flags) ? (flags & hist_flags) : hist_flags;
     hepacc_plan* p = new (std::nothrow) hepacc_plan();
@@ -423,6 +437,12 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
         leps += (b.leptons_per_event > 0 ? b.leptons_per_event : 1.5) * n;
         events += n;
         p->max_events = std::max<int64_t>(p->max_events, b.n_events);
+    }
+    if ((flags & HEPACC_PLAN_VALIDATE) || debug_checks()) {
+        for (int i = 0; i < n_samples; ++i) {
+            st = check_batch_offsets(&samples[i], reinterpret_cast<cudaStream_t>(stream));
+            if (st != HEPACC_OK) return drop(fail(st, "sample %d: %s", i, hepacc_last_error()));
+        }
     }
     p->kin = samples[0].kin_type;
     p->btag = samples[0].btag_type;

@@ -27,6 +27,13 @@ struct DeviceInfo {
 };
 DeviceInfo device_info();
 
+// Debug checks before chain launches (environment variable HEPACC_DEBUG set
+// and not 0), and the offsets check they run: a kernel over the offsets,
+// then a wait for it; HEPACC_ERR_DEVICE_CHECK when offsets[0] < 0 or the
+// offsets decrease.
+bool debug_checks();
+hepacc_status check_offsets_nondecreasing(const void* offsets, hepacc_dtype ot, int64_t n, cudaStream_t s);
+
 inline bool is_float_type(hepacc_dtype t) { return t == HEPACC_F32 || t == HEPACC_F16 || t == HEPACC_BF16; }
 inline bool is_offsets_type(hepacc_dtype t) { return t == HEPACC_I32 || t == HEPACC_I64; }
 inline size_t dtype_size(hepacc_dtype t) {

@@ -3,6 +3,7 @@
 // object selection, scaling and weighted histogram filling, with their C-ABI
 // entry points.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <unordered_map>
 
@@ -10,6 +11,17 @@
 #include "hepacc_tiles.cuh"
 
 namespace hepacc {
+
+// Debug checks of the offsets before a chain launch: on when the
+// environment variable HEPACC_DEBUG is set to a value other than 0, or when
+// the caller asks (plans).
+bool debug_checks() {
+    static const bool on = [] {
+        const char* v = std::getenv("HEPACC_DEBUG");
+        return v != nullptr && v[0] != '\0' && !(v[0] == '0' && v[1] == '\0');
+    }();
+    return on;
+}
 
 unsigned int tu_error_ops(bool clear) {
     unsigned int v = 0;
@@ -549,6 +561,17 @@ __global__ void k_validate(const OffT* off, int64_t n, int64_t m, unsigned long 
     }
 }
 
+// Offsets check that reports through the device error word: bit 1 when
+// offsets[0] < 0 or offsets decrease anywhere.
+template <typename OffT>
+__global__ void k_check_offsets(const OffT* off, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t a = ldoff(off, i), b = ldoff(off, i + 1);
+        if (b < a || (i == 0 && a < 0)) atomicOr(&g_device_error, kErrCheck);
+    }
+}
+
 // One thread waits on an mbarrier that is never completed (bounded wait).
 __global__ void k_wait_timeout(long long limit_cycles) {
     __shared__ uint64_t bar;
@@ -1004,6 +1027,39 @@ hepacc_status hepacc_selftest_wait_timeout(int64_t limit_cycles, hepacc_stream s
     HEPACC_CHECK_LAUNCH("selftest launch");
     return HEPACC_OK;
 }
+
+}  // extern "C"
+
+namespace hepacc {
+
+// Launches the offsets check, waits for it and reads (and clears) the check
+// bit of this translation unit's error word: HEPACC_ERR_DEVICE_CHECK if the
+// offsets are negative at the start or decrease.
+hepacc_status check_offsets_nondecreasing(const void* offsets, hepacc_dtype ot, int64_t n, cudaStream_t s) {
+    if (n <= 0) return HEPACC_OK;
+    if (!offsets) return fail(HEPACC_ERR_INVALID_ARG, "offsets are required");
+    hepacc_status st = with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
+        using O = typename decltype(ot_tag)::type;
+        k_check_offsets<O><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const O*>(offsets), n);
+        HEPACC_CHECK_LAUNCH("offsets check launch");
+        return HEPACC_OK;
+    });
+    if (st != HEPACC_OK) return st;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "offsets check");
+    unsigned int v = 0;
+    cudaMemcpyFromSymbol(&v, g_device_error, sizeof v);
+    if (v & kErrCheck) {
+        const unsigned int keep = v & ~kErrCheck;
+        cudaMemcpyToSymbol(g_device_error, &keep, sizeof keep);
+        return fail(HEPACC_ERR_DEVICE_CHECK, "offsets are negative at the start or decrease");
+    }
+    return HEPACC_OK;
+}
+
+}  // namespace hepacc
+
+extern "C" {
 
 hepacc_status hepacc_validate_offsets(const void* offsets, hepacc_dtype ot, int64_t n, int64_t content_len,
                                       int64_t* first_bad, hepacc_stream stream) {

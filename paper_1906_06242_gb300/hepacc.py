@@ -493,6 +493,8 @@ def hepacc_run_chain(batch: DeviceBatch, cfg: ChainConfig, out: ChainOutputs, st
 
 PLAN_AUTOTUNE = 1
 PLAN_GRAPH = 2
+PLAN_HIST_BLOCK, PLAN_HIST_CLUSTER8, PLAN_HIST_CLUSTER16, PLAN_HIST_GLOBAL = 4, 8, 16, 32
+PLAN_VALIDATE = 64
 
 
 class Plan:
