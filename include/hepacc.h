@@ -286,9 +286,9 @@ typedef struct {
     const float *el_iso;
     const uint8_t *el_tight;
     const float *weight;
-    /* Mean jets and leptons (muons plus electrons) per event, used only to
-     * size the shared-memory staging; 0 selects 6 and 1.5. */
-    float jets_per_event, leptons_per_event;
+    /* Mean jets, muons and electrons per event, used only to size the
+     * shared-memory staging of each collection; 0 selects 6, 1 and 1. */
+    float jets_per_event, muons_per_event, electrons_per_event;
 } hepacc_event_batch;
 
 /* Cuts, jet-pt scale variations and the 20 histograms. HOST memory: the call

@@ -131,14 +131,14 @@ void make_sample(const hepacc_event_batch* b, const hepacc_chain_outputs* out, S
 // flags, a 64-entry pair list and the event summaries per warp, and the
 // histograms of the placement (all of them in H_SMEM, a
 // 1/cluster slice in H_CLUSTER, none in H_GLOBAL). Returns whether it fits.
-bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_t kes, size_t bes,
+bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_m, double lam_e, size_t kes, size_t bes,
                 int blocks_per_sm, const ChainParams& P, Layout& L) {
     std::memset(&L, 0, sizeof L);
     auto cap_of = [&](double lam) {
         const double m = E * lam;
         return static_cast<uint32_t>(((static_cast<size_t>(m + 4.0 * std::sqrt(m) + 64.0)) + 31) & ~size_t(31));
     };
-    const uint32_t cj = cap_of(lam_j), cl = cap_of(lam_l);
+    const uint32_t cj = cap_of(lam_j), cm = cap_of(lam_m), ce = cap_of(lam_e);
     uint32_t off = 0;
     auto add = [&](int c, size_t es, int coll, uint32_t cap) {
         ColSpec& cs = L.col[c];
@@ -154,16 +154,16 @@ bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_l, size_
     add(J_PHI, kes, 0, cj);
     add(J_MASS, kes, 0, cj);
     add(J_BTAG, bes, 0, cj);
-    add(M_PT, kes, 1, cl);
-    add(M_ETA, kes, 1, cl);
-    add(M_PHI, kes, 1, cl);
-    add(M_ISO, 4, 1, cl);
-    add(M_TIGHT, 1, 1, cl);
-    add(E_PT, kes, 2, cl);
-    add(E_ETA, kes, 2, cl);
-    add(E_PHI, kes, 2, cl);
-    add(E_ISO, 4, 2, cl);
-    add(E_TIGHT, 1, 2, cl);
+    add(M_PT, kes, 1, cm);
+    add(M_ETA, kes, 1, cm);
+    add(M_PHI, kes, 1, cm);
+    add(M_ISO, 4, 1, cm);
+    add(M_TIGHT, 1, 1, cm);
+    add(E_PT, kes, 2, ce);
+    add(E_ETA, kes, 2, ce);
+    add(E_PHI, kes, 2, ce);
+    add(E_ISO, 4, 2, ce);
+    add(E_TIGHT, 1, 2, ce);
     auto up = [](size_t x) { return static_cast<uint32_t>((x + 127) & ~size_t(127)); };
     // every region starts on a 16-byte boundary (8-byte fields live in
     // several of them)
@@ -240,7 +240,8 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     make_sample(b, out, B.s[0]);
 
     const double lam_j = b->jets_per_event > 0 ? b->jets_per_event : 6.0;
-    const double lam_l = b->leptons_per_event > 0 ? b->leptons_per_event : 1.5;
+    const double lam_m = b->muons_per_event > 0 ? b->muons_per_event : 1.0;
+    const double lam_e = b->electrons_per_event > 0 ? b->electrons_per_event : 1.0;
     const size_t kes = dtype_size(b->kin_type), bes = dtype_size(b->btag_type);
     Layout L;
     int E = 0, hmode = H_SMEM;
@@ -249,10 +250,10 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     // ones (smaller blocks measured slower than global histograms)
     for (int bps = kMinBlocks; bps >= 1 && E == 0; bps = bps > 1 ? 1 : 0) {
         for (int e = kMaxThreads; e >= 64 && E == 0; e -= 32) {
-            if (layout_for(e, H_SMEM, 1, lam_j, lam_l, kes, bes, bps, P, L)) {
+            if (layout_for(e, H_SMEM, 1, lam_j, lam_m, lam_e, kes, bes, bps, P, L)) {
                 E = e;
                 hmode = H_SMEM;
-            } else if (layout_for(e, H_GLOBAL, 1, lam_j, lam_l, kes, bes, bps, P, L)) {
+            } else if (layout_for(e, H_GLOBAL, 1, lam_j, lam_m, lam_e, kes, bes, bps, P, L)) {
                 E = e;
                 hmode = H_GLOBAL;
             }
@@ -418,7 +419,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     };
     hepacc_status st = make_params(cfg, p->P);
     if (st != HEPACC_OK) return drop(st);
-    double jets = 0, leps = 0, events = 0;
+    double jets = 0, mus = 0, els = 0, events = 0;
     p->max_events = 0;
     for (int i = 0; i < n_samples; ++i) {
         const hepacc_event_batch& b = samples[i];
@@ -434,7 +435,8 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
             return drop(fail(HEPACC_ERR_DTYPE, "plans take F32 btag with F32 kinematics, F16 btag with half kinematics"));
         const double n = static_cast<double>(b.n_events);
         jets += (b.jets_per_event > 0 ? b.jets_per_event : 6.0) * n;
-        leps += (b.leptons_per_event > 0 ? b.leptons_per_event : 1.5) * n;
+        mus += (b.muons_per_event > 0 ? b.muons_per_event : 1.0) * n;
+        els += (b.electrons_per_event > 0 ? b.electrons_per_event : 1.0) * n;
         events += n;
         p->max_events = std::max<int64_t>(p->max_events, b.n_events);
     }
@@ -447,7 +449,8 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     p->kin = samples[0].kin_type;
     p->btag = samples[0].btag_type;
     const double lam_j = events > 0 ? jets / events : 6.0;
-    const double lam_l = events > 0 ? leps / events : 1.5;
+    const double lam_m = events > 0 ? mus / events : 1.0;
+    const double lam_e = events > 0 ? els / events : 1.0;
     p->outs.assign(outputs, outputs + n_samples);
     for (int i0 = 0; i0 < n_samples; i0 += kMaxSamples) {
         BatchDesc B;
@@ -472,7 +475,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
         const int bps = m[0] == H_GLOBAL ? kMinBlocks : kMinBlocksBatched;
         for (int e = emax; e >= 64 && (allowed & m[2]); e -= 32) {
             Candidate c;
-            if (layout_for(e, m[0], m[1], lam_j, lam_l, kes, bes, bps, p->P, c.L)) {
+            if (layout_for(e, m[0], m[1], lam_j, lam_m, lam_e, kes, bes, bps, p->P, c.L)) {
                 c.hmode = m[0];
                 c.cluster = m[1];
                 c.block = e;

@@ -326,7 +326,7 @@ class EventBatchC(ctypes.Structure):
                 ("el_pt", _c_void_p), ("el_eta", _c_void_p), ("el_phi", _c_void_p), ("el_iso", _c_void_p),
                 ("el_tight", _c_void_p),
                 ("weight", _c_void_p), ("jets_per_event", ctypes.c_float),
-                ("leptons_per_event", ctypes.c_float)]
+                ("muons_per_event", ctypes.c_float), ("electrons_per_event", ctypes.c_float)]
 
 
 class ChainConfigC(ctypes.Structure):
@@ -400,7 +400,8 @@ class DeviceBatch:
         c.weight = _addr(self.weight)
         n = max(1, self.n_events)
         c.jets_per_event = self.cols["jet_pt"].numel() / n
-        c.leptons_per_event = (self.cols["mu_pt"].numel() + self.cols["el_pt"].numel()) / n
+        c.muons_per_event = self.cols["mu_pt"].numel() / n
+        c.electrons_per_event = self.cols["el_pt"].numel() / n
         self._c = c
         return c
 
