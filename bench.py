@@ -308,6 +308,7 @@ def main():
     extra = {}
     if not args.no_extra and rank == 0:
         extra = secondary_forms(H, synth, batch, torch, stream)
+        extra["kernels"] = kernel_forms(H, batch, torch, stream)
         extra.update(batched_forms(H, synth, torch, stream, args.batched_scale))
         if args.dense_events > 0:
             extra.update(dense_forms(H, synth, torch, stream, args.dense_events))
@@ -394,6 +395,64 @@ def secondary_forms(H, synth, batch, torch, stream):
                                "passing_f32": int(ref_pass.sum().item()),
                                "hist_count_l1_vs_f32": l1}
         del dh, pe
+    return res
+
+
+def kernel_forms(H, batch, torch, stream):
+    """Each per-operation kernel alone on the 10M workload's device columns:
+    device time, algorithmic bytes (every array the call must read or write,
+    once) and the fraction of the measured HBM copy bandwidth."""
+    import math
+    hbm, _ = peaks()
+    db = H.DeviceBatch.from_host(batch)
+    C = db.cols
+    jo, mo = db.offsets["jet"], db.offsets["mu"]
+    n, mj, mm = batch.n_events, C["jet_pt"].numel(), C["mu_pt"].numel()
+    ob = 8 * (n + 1)
+    dev = "cuda"
+    out_f = torch.zeros(n, dtype=torch.float32, device=dev)
+    out_f2 = torch.zeros(n, dtype=torch.float32, device=dev)
+    idx = torch.zeros(n, dtype=torch.int32, device=dev)
+    idx3 = torch.zeros((n, 3), dtype=torch.int32, device=dev)
+    mask_j = torch.empty(mj, dtype=torch.uint8, device=dev)
+    mask_m = torch.ones(mm, dtype=torch.uint8, device=dev)
+    edges = torch.from_numpy(H.hist_edges(20.0, 500.0, 100)).to(dev)
+    counts = torch.zeros(102, dtype=torch.int64, device=dev)
+    sumw = torch.zeros(102, dtype=torch.float64, device=dev)
+    sumw2 = torch.zeros(102, dtype=torch.float64, device=dev)
+    n_first = int((np.diff(batch.jet_offsets) > 0).sum())   # events with a first jet
+    ops = {
+        "sum_in_offsets": (lambda: H.hepacc_sum_in_offsets(C["jet_pt"], jo, out=out_f, stream=stream),
+                           4 * mj + ob + 8 * n),
+        "max_in_offsets": (lambda: H.hepacc_max_in_offsets(C["jet_pt"], jo, out=out_f, arg=idx, stream=stream),
+                           4 * mj + ob + 8 * n),
+        "get_in_offsets": (lambda: H.hepacc_get_in_offsets(C["jet_pt"], jo, 0, out=out_f, index=idx, stream=stream),
+                           ob + 4 * n_first + 8 * n),
+        "select_range": (lambda: H.hepacc_select_range(C["jet_pt"], lo=30.0, hi=math.inf, mask_out=mask_j,
+                                                       stream=stream), 5 * mj),
+        "mask_deltar": (lambda: H.hepacc_mask_deltar(C["jet_eta"], C["jet_phi"], jo, C["mu_eta"], C["mu_phi"], mo,
+                                                     mask2=mask_m, dr2_cut=0.16, mask1_out=mask_j, stream=stream),
+                        8 * mj + 9 * mm + 2 * ob + mj),
+        "fill_histogram": (lambda: H.hepacc_fill_histogram(C["jet_pt"], edges, counts=counts, sumw=sumw,
+                                                           sumw2=sumw2, stream=stream), 4 * mj),
+        "max_pt_trijet": (lambda: H.hepacc_max_pt_trijet(C["jet_pt"], C["jet_eta"], C["jet_phi"], C["jet_mass"], jo,
+                                                         out_mass=out_f, out_pt=out_f2, out_idx3=idx3,
+                                                         stream=stream), 16 * mj + ob + 20 * n),
+    }
+    res = {}
+    for name, (fn, nbytes) in ops.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(20):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / 20
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "algorithmic_bytes": int(nbytes), "gbs": gbs, "hbm_frac": gbs / hbm}
     return res
 
 

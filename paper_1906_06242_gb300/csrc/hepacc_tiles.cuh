@@ -199,4 +199,37 @@ __device__ __forceinline__ void tile_loop(const StageSpec<NC>& spec, const OffT*
     }
 }
 
+// Lane = event over [0, n) with a grid-stride loop and no staging: each
+// event's elements are read straight from global memory through the cache
+// (the events of a warp are adjacent, so its loads share cache lines). For
+// kernels whose per-event work is a short scan this costs fewer instructions
+// per event than the staged tiles. body(cols, ranges) as for tile_loop, with
+// a GlobCols and the ranges of one event (rs = 0).
+template <typename OffT, int NCOLL, int NC, typename Body>
+__device__ __forceinline__ void event_loop(const StageSpec<NC>& spec, const OffT* const (&offs)[NCOLL], int64_t n,
+                                           Body&& body) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n; e += stride) {
+        TileRanges<NCOLL> r;
+        r.e = e;
+        r.valid = true;
+#pragma unroll
+        for (int c = 0; c < NCOLL; ++c) {
+            const int64_t a = ldoff(offs[c], e);
+            r.S[c] = a;
+            r.rs[c] = 0;
+            r.rt[c] = static_cast<int>(ldoff(offs[c], e + 1) - a);
+        }
+        GlobCols<NC> gc;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            gc.p[c] = nullptr;
+            if (c >= spec.ncol || spec.col[c].base == nullptr) continue;
+            const ColSpec& col = spec.col[c];
+            gc.p[c] = col.base + static_cast<uintptr_t>(r.S[col.coll]) * col.es;
+        }
+        body(gc, r);
+    }
+}
+
 }  // namespace hepacc

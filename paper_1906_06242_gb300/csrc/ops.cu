@@ -62,13 +62,13 @@ __device__ __forceinline__ float acc_add<float, __nv_bfloat16>(float a, __nv_bfl
 }
 
 // sum_in_offsets (Listing 1): out[e] += masked elements in element order.
-// Columns: 0 = content, 1 = mask_content.
+// Columns: 0 = content, 1 = mask_content. Lane = event, no staging.
 template <typename T, typename OffT, typename OutT>
 __global__ void __launch_bounds__(kBlock) k_sum(Spec spec, const OffT* off, int64_t n,
                                                 const uint8_t* __restrict__ mask_rows, OutT* __restrict__ out) {
     const OffT* const offs[1] = {off};
     const bool hm = spec.col[1].base != nullptr;
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+    event_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
         if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
         using A = typename Acc<T>::type;
         A acc = static_cast<A>(out[r.e]);
@@ -81,13 +81,14 @@ __global__ void __launch_bounds__(kBlock) k_sum(Spec spec, const OffT* off, int6
 }
 
 // max/min_in_offsets: first occurrence of the extreme non-NaN masked value.
+// Lane = event, no staging.
 template <typename T, typename OffT, bool MAX>
 __global__ void __launch_bounds__(kBlock) k_minmax(Spec spec, const OffT* off, int64_t n,
                                                    const uint8_t* __restrict__ mask_rows, float empty,
                                                    float* __restrict__ out, int32_t* __restrict__ arg) {
     const OffT* const offs[1] = {off};
     const bool hm = spec.col[1].base != nullptr;
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+    event_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
         if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
         int bi = -1;
         float best = empty;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) k_minmax(Spec spec, const OffT* off, i
     });
 }
 
-// get_in_offsets: the n-th masked-in element.
+// get_in_offsets: the n-th masked-in element. Lane = event, no staging.
 template <typename T, typename OffT>
 __global__ void __launch_bounds__(kBlock) k_get(Spec spec, const OffT* off, int64_t n,
                                                 const int32_t* __restrict__ nth, int32_t nth_scalar,
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) k_get(Spec spec, const OffT* off, int6
                                                 float* __restrict__ out, int32_t* __restrict__ oidx) {
     const OffT* const offs[1] = {off};
     const bool hm = spec.col[1].base != nullptr;
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+    event_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
         if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
         const int64_t want = nth ? nth[r.e] : nth_scalar;
         int64_t seen = 0;
@@ -465,6 +466,65 @@ __global__ void __launch_bounds__(kBlock) k_select(const T* x, int64_t n, float 
     }
 }
 
+// Vector forms of the elementwise kernels: each thread takes whole 16-byte
+// chunks of the content (V = 16 / sizeof(T) elements) and the matching V
+// bytes of the masks or 4 V bytes of the output, so that every load and
+// store is as wide as the data allows; the last n % V elements go one by
+// one. The host takes them when every pointer is aligned to its access.
+template <int V> struct VBytes;
+template <> struct VBytes<4> { using type = uint32_t; };
+template <> struct VBytes<8> { using type = uint2; };
+template <> struct VBytes<16> { using type = uint4; };
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_select_vec(const T* x, int64_t n, float scale, float lo, float hi,
+                                                       int use_abs, const uint8_t* min, uint8_t* mout) {
+    constexpr int V = 16 / static_cast<int>(sizeof(T));
+    using MV = typename VBytes<V>::type;
+    const int64_t nv = n / V;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    for (int64_t c = t0; c < nv; c += stride) {
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(x) + c);
+        const T* v = reinterpret_cast<const T*>(&raw);
+        MV inm;
+        if (min) inm = __ldg(reinterpret_cast<const MV*>(min) + c);
+        const uint8_t* in = reinterpret_cast<const uint8_t*>(&inm);
+        MV o;
+        uint8_t* ob = reinterpret_cast<uint8_t*>(&o);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            float f = __fmul_rn(Elem<T>::f(v[i]), scale);
+            if (use_abs) f = fabsf(f);
+            ob[i] = ((!min || in[i] != 0) && f > lo && f < hi) ? 1 : 0;
+        }
+        reinterpret_cast<MV*>(mout)[c] = o;
+    }
+    for (int64_t j = nv * V + t0; j < n; j += stride) {
+        float f = __fmul_rn(ldf(x, j), scale);
+        if (use_abs) f = fabsf(f);
+        mout[j] = ((!min || min[j] != 0) && f > lo && f < hi) ? 1 : 0;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_scale_vec(const T* x, int64_t n, float s, float* out) {
+    constexpr int V = 16 / static_cast<int>(sizeof(T));
+    const int64_t nv = n / V;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    for (int64_t c = t0; c < nv; c += stride) {
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(x) + c);
+        const T* v = reinterpret_cast<const T*>(&raw);
+        float4* o = reinterpret_cast<float4*>(out + c * V);
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q)
+            o[q] = make_float4(__fmul_rn(Elem<T>::f(v[4 * q]), s), __fmul_rn(Elem<T>::f(v[4 * q + 1]), s),
+                               __fmul_rn(Elem<T>::f(v[4 * q + 2]), s), __fmul_rn(Elem<T>::f(v[4 * q + 3]), s));
+    }
+    for (int64_t j = nv * V + t0; j < n; j += stride) out[j] = __fmul_rn(ldf(x, j), s);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_scale(const T* x, int64_t n, float s, float* out) {
     for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
@@ -633,6 +693,8 @@ hepacc_status tile_grid(K kernel, size_t smem, int64_t ntiles, int* grid) {
     return HEPACC_OK;
 }
 
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
 inline int flat_grid(int64_t n) {
     const DeviceInfo di = device_info();
     const int64_t want = (n + kBlock - 1) / kBlock;
@@ -699,6 +761,14 @@ hepacc_status with_offsets_type(hepacc_dtype t, F&& f) {
     }
 }
 
+// Kernels on event_loop: no shared memory, one thread per event at a time.
+template <typename K, typename... Args>
+hepacc_status launch_flat(K kernel, const Spec& spec, int64_t n, cudaStream_t stream, Args... args) {
+    kernel<<<flat_grid(n), kBlock, 0, stream>>>(spec, args...);
+    HEPACC_CHECK_LAUNCH("kernel launch");
+    return HEPACC_OK;
+}
+
 template <typename K, typename... Args>
 hepacc_status launch_tiles(K kernel, const Spec& spec, int64_t n, cudaStream_t stream, Args... args) {
     const size_t smem = static_cast<size_t>(stage_bytes_per_warp(spec)) * (kBlock / 32);
@@ -734,7 +804,7 @@ hepacc_status hepacc_sum_in_offsets(const void* content, hepacc_dtype ct, const 
                 using T = typename decltype(t)::type;
                 b.add(content, sizeof(T), 0);
                 b.add(mask_content, 1, 0);
-                return launch_tiles(k_sum<T, O, float>, b.done(), n, s, off, n, mask_rows, static_cast<float*>(out));
+                return launch_flat(k_sum<T, O, float>, b.done(), n, s, off, n, mask_rows, static_cast<float*>(out));
             });
         }
         auto run_int = [&](auto t) -> hepacc_status {
@@ -742,9 +812,9 @@ hepacc_status hepacc_sum_in_offsets(const void* content, hepacc_dtype ct, const 
             b.add(content, sizeof(T), 0);
             b.add(mask_content, 1, 0);
             if (out_t == HEPACC_I64)
-                return launch_tiles(k_sum<T, O, int64_t>, b.done(), n, s, off, n, mask_rows, static_cast<int64_t*>(out));
+                return launch_flat(k_sum<T, O, int64_t>, b.done(), n, s, off, n, mask_rows, static_cast<int64_t*>(out));
             if (out_t == HEPACC_I32 && ct != HEPACC_I64)
-                return launch_tiles(k_sum<T, O, int32_t>, b.done(), n, s, off, n, mask_rows, static_cast<int32_t*>(out));
+                return launch_flat(k_sum<T, O, int32_t>, b.done(), n, s, off, n, mask_rows, static_cast<int32_t*>(out));
             return fail(HEPACC_ERR_DTYPE, "integer content sums into I32 or I64 (I64 content: I64)");
         };
         switch (ct) {
@@ -772,9 +842,9 @@ static hepacc_status minmax_impl(bool is_max, const void* content, hepacc_dtype 
             b.add(content, sizeof(T), 0);
             b.add(mask_content, 1, 0);
             if (is_max)
-                return launch_tiles(k_minmax<T, O, true>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows,
+                return launch_flat(k_minmax<T, O, true>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows,
                                     empty, out, arg);
-            return launch_tiles(k_minmax<T, O, false>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows,
+            return launch_flat(k_minmax<T, O, false>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows,
                                 empty, out, arg);
         });
     });
@@ -807,7 +877,7 @@ hepacc_status hepacc_get_in_offsets(const void* content, hepacc_dtype ct, const 
             SpecBuilder b;
             b.add(content, sizeof(T), 0);
             b.add(mask_content, 1, 0);
-            return launch_tiles(k_get<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, nth, nth_scalar,
+            return launch_flat(k_get<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, nth, nth_scalar,
                                 mask_rows, dflt, out, oidx);
         });
     });
@@ -845,8 +915,14 @@ hepacc_status hepacc_select_range(const void* content, hepacc_dtype ct, int64_t 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return with_value_type(ct, [&](auto t) -> hepacc_status {
         using T = typename decltype(t)::type;
-        k_select<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, lo, hi, use_abs, mask_in,
-                                                    mask_out);
+        constexpr int V = 16 / static_cast<int>(sizeof(T));
+        const bool vec = aligned(content, 16) && aligned(mask_out, V) && (!mask_in || aligned(mask_in, V));
+        if (vec)
+            k_select_vec<T><<<flat_grid((n + V - 1) / V), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, lo,
+                                                                          hi, use_abs, mask_in, mask_out);
+        else
+            k_select<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, lo, hi, use_abs,
+                                                        mask_in, mask_out);
         HEPACC_CHECK_LAUNCH("select_range launch");
         return HEPACC_OK;
     });
@@ -860,7 +936,11 @@ hepacc_status hepacc_scale(const void* content, hepacc_dtype ct, int64_t n, floa
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return with_float_type(ct, [&](auto t) -> hepacc_status {
         using T = typename decltype(t)::type;
-        k_scale<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, out);
+        constexpr int V = 16 / static_cast<int>(sizeof(T));
+        if (aligned(content, 16) && aligned(out, 16))
+            k_scale_vec<T><<<flat_grid((n + V - 1) / V), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, out);
+        else
+            k_scale<T><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const T*>(content), n, scale, out);
         HEPACC_CHECK_LAUNCH("scale launch");
         return HEPACC_OK;
     });

@@ -159,6 +159,34 @@ def test_select_and_scale(H, orc, fmt):
     np.testing.assert_array_equal(host(H.hepacc_scale(dev(xh, ofmt), 1.03)), want)
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.int8, np.int32, np.float32])
+@pytest.mark.parametrize("shift", [0, 1, 3])
+def test_select_range_vector_and_unaligned(H, orc, dtype, shift):
+    # the 16-byte vector path (aligned views, ragged tail) and the element
+    # path (views starting off a 16-byte boundary)
+    rng = np.random.default_rng(13)
+    n = 50_011 + shift
+    if dtype == np.float32:
+        x = rng.normal(30, 20, n).astype(np.float32)
+    else:
+        x = rng.integers(-60 if dtype != np.uint8 else 0, 120, n).astype(dtype)
+    mi = (rng.random(n) < 0.7).astype(np.uint8)
+    want = orc.select_range(np.ascontiguousarray(x[shift:]), 10.0, 60.0, 1.0, False, mi[shift:])
+    got = H.hepacc_select_range(dev(x)[shift:], 10.0, 60.0, 1.0, False, dev(mi)[shift:])
+    np.testing.assert_array_equal(host(got), want)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+@pytest.mark.parametrize("shift", [0, 1, 5])
+def test_scale_vector_and_unaligned(H, orc, fmt, shift):
+    rng = np.random.default_rng(14)
+    x = rng.normal(30, 5, 40_007).astype(np.float32)
+    xh = x if fmt == "f32" else synth.to_half_bits(x, fmt)
+    ofmt = None if fmt == "f32" else fmt
+    want = orc.scale(np.ascontiguousarray(xh[shift:]), 0.97, fmt=ofmt)
+    np.testing.assert_array_equal(host(H.hepacc_scale(dev(xh, ofmt)[shift:], 0.97)), want)
+
+
 @pytest.mark.parametrize("fmt,od", [("f32", np.int64), ("bf16", np.int32), ("f16", np.int64)])
 def test_mask_deltar(H, orc, fmt, od):
     b = synth.generate(50021, 31, lam_mu=2.0, offset_dtype=od)
