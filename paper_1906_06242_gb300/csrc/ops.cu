@@ -36,7 +36,6 @@ unsigned int tu_error_ops(bool clear) {
 namespace {
 
 constexpr int kBlock = 256;             // 8 warps
-constexpr int kCapElems = 512;          // stage capacity per column, elements (32 events x 16)
 constexpr int NC = 6;                   // columns per stage at most
 using Spec = StageSpec<NC>;
 
@@ -135,14 +134,14 @@ __global__ void __launch_bounds__(kBlock) k_get(Spec spec, const OffT* off, int6
 }
 
 // mask_deltar_first. Columns: 0 eta1, 1 phi1, 2 mask1_in (collection 0);
-// 3 eta2, 4 phi2, 5 mask2 (collection 1).
+// 3 eta2, 4 phi2, 5 mask2 (collection 1). Lane = event, no staging.
 template <typename T1, typename T2, typename OffT>
 __global__ void __launch_bounds__(kBlock) k_deltar(Spec spec, const OffT* off1, const OffT* off2, int64_t n,
                                                    const uint8_t* __restrict__ mask_rows, float cut,
                                                    uint8_t* __restrict__ mask_out) {
     const OffT* const offs[2] = {off1, off2};
     const bool h1 = spec.col[2].base != nullptr, h2 = spec.col[5].base != nullptr;
-    tile_loop<OffT, 2, NC>(spec, offs, n, [&](const auto& C, const TileRanges<2>& r) {
+    event_loop<OffT, 2, NC>(spec, offs, n, [&](const auto& C, const TileRanges<2>& r) {
         if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
         for (int i = r.rs[0]; i < r.rt[0]; ++i) {
             bool keep = h1 ? C.template ld<uint8_t>(2, i) != 0 : true;
@@ -165,7 +164,7 @@ __global__ void __launch_bounds__(kBlock) k_deltar(Spec spec, const OffT* off1, 
 }
 
 // Trijet: max |sum pT| over triplets of masked-in objects, its mass.
-// Columns: 0 pt, 1 eta, 2 phi, 3 mass, 4 mask.
+// Columns: 0 pt, 1 eta, 2 phi, 3 mass, 4 mask. Lane = event, no staging.
 constexpr int kTriLocal = 24;
 
 template <typename T, typename OffT>
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_trijet(Spec spec, const OffT* off, i
                                                    float* __restrict__ opt, int32_t* __restrict__ oidx) {
     const OffT* const offs[1] = {off};
     const bool hm = spec.col[4].base != nullptr;
-    tile_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
+    event_loop<OffT, 1, NC>(spec, offs, n, [&](const auto& C, const TileRanges<1>& r) {
         if (!r.valid || (mask_rows && !mask_rows[r.e])) return;
         auto pt_of = [&](int i) { return Elem<T>::f(C.template ld<T>(0, i)); };
         auto phi_of = [&](int i) { return Elem<T>::f(C.template ld<T>(2, i)); };
@@ -705,7 +704,7 @@ struct SpecBuilder {
     Spec s{};
     uint32_t off = 0;
     SpecBuilder() { s.ncol = 0; }
-    void add(const void* base, size_t es, int coll, int cap_elems = kCapElems) {
+    void add(const void* base, size_t es, int coll, int cap_elems = 0) {
         ColSpec& c = s.col[s.ncol++];
         c.base = static_cast<const unsigned char*>(base);
         c.es = static_cast<uint32_t>(es);
@@ -769,16 +768,6 @@ hepacc_status launch_flat(K kernel, const Spec& spec, int64_t n, cudaStream_t st
     return HEPACC_OK;
 }
 
-template <typename K, typename... Args>
-hepacc_status launch_tiles(K kernel, const Spec& spec, int64_t n, cudaStream_t stream, Args... args) {
-    const size_t smem = static_cast<size_t>(stage_bytes_per_warp(spec)) * (kBlock / 32);
-    int grid = 0;
-    hepacc_status st = tile_grid(kernel, smem, (n + kTile - 1) / kTile, &grid);
-    if (st != HEPACC_OK) return st;
-    kernel<<<grid, kBlock, smem, stream>>>(spec, args...);
-    HEPACC_CHECK_LAUNCH("kernel launch");
-    return HEPACC_OK;
-}
 
 }  // namespace
 }  // namespace hepacc
@@ -967,7 +956,7 @@ hepacc_status hepacc_mask_deltar(const void* eta1, const void* phi1, hepacc_dtyp
                 b.add(eta2, sizeof(T2), 1, 256);
                 b.add(phi2, sizeof(T2), 1, 256);
                 b.add(mask2, 1, 1, 256);
-                return launch_tiles(k_deltar<T1, T2, O>, b.done(), n, s, static_cast<const O*>(off1),
+                return launch_flat(k_deltar<T1, T2, O>, b.done(), n, s, static_cast<const O*>(off1),
                                     static_cast<const O*>(off2), n, mask_rows, dr2_cut, mask1_out);
             });
         });
@@ -1012,7 +1001,7 @@ hepacc_status hepacc_max_pt_trijet(const void* pt, const void* eta, const void* 
             b.add(phi, sizeof(T), 0);
             b.add(mass, sizeof(T), 0);
             b.add(mask_content, 1, 0);
-            return launch_tiles(k_trijet<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows, out_mass,
+            return launch_flat(k_trijet<T, O>, b.done(), n, s, static_cast<const O*>(offsets), n, mask_rows, out_mass,
                                 out_pt, out_idx3);
         });
     });
