@@ -244,21 +244,13 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     const double lam_e = b->electrons_per_event > 0 ? b->electrons_per_event : 1.0;
     const size_t kes = dtype_size(b->kin_type), bes = dtype_size(b->btag_type);
     Layout L;
-    int E = 0, hmode = H_SMEM;
-    // blocks per SM as built for, else one; the largest block that fits,
-    // with block-private histograms when they fit beside it, else global
-    // ones (smaller blocks measured slower than global histograms)
-    for (int bps = kMinBlocks; bps >= 1 && E == 0; bps = bps > 1 ? 1 : 0) {
-        for (int e = kMaxThreads; e >= 64 && E == 0; e -= 32) {
-            if (layout_for(e, H_SMEM, 1, lam_j, lam_m, lam_e, kes, bes, bps, P, L)) {
-                E = e;
-                hmode = H_SMEM;
-            } else if (layout_for(e, H_GLOBAL, 1, lam_j, lam_m, lam_e, kes, bes, bps, P, L)) {
-                E = e;
-                hmode = H_GLOBAL;
-            }
-        }
-    }
+    int E = 0, hmode = H_GLOBAL;
+    // blocks per SM as built for, else one; the largest block that fits.
+    // Histograms in global memory: measured faster here than block-private
+    // shared-memory copies, whose fill serialises each histogram on one lane
+    for (int bps = kMinBlocks; bps >= 1 && E == 0; bps = bps > 1 ? 1 : 0)
+        for (int e = kMaxThreads; e >= 64 && E == 0; e -= 32)
+            if (layout_for(e, H_GLOBAL, 1, lam_j, lam_m, lam_e, kes, bes, bps, P, L)) E = e;
     if (E == 0) return fail(HEPACC_ERR_INVALID_ARG, "chain stage buffers do not fit in shared memory");
 
     LaunchArgs a;

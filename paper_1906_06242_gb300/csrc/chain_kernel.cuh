@@ -1125,11 +1125,8 @@ hepacc_status run_typed(const LaunchArgs& a) {
     auto go = [&](auto bt, auto ot) -> hepacc_status {
         using BT = typename decltype(bt)::type;
         using O = typename decltype(ot)::type;
-        if (a.debug) {
-            if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, true, H_SMEM, F_SINGLE>, a);
-            return launch_chain(k_chain<KT, BT, O, true, H_GLOBAL, F_SINGLE>, a);
-        }
-        if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, O, false, H_SMEM, F_SINGLE>, a);
+        if (a.hmode != H_GLOBAL) return fail(HEPACC_ERR_INVALID_ARG, "single-sample launches fill global histograms");
+        if (a.debug) return launch_chain(k_chain<KT, BT, O, true, H_GLOBAL, F_SINGLE>, a);
         return launch_chain(k_chain<KT, BT, O, false, H_GLOBAL, F_SINGLE>, a);
     };
     auto with_o = [&](auto bt) -> hepacc_status {
