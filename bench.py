@@ -166,6 +166,39 @@ def cpu_baseline(batch, n_sample, shifts=(0,)):
                       f"{dt:.2f} s single-threaded"}
 
 
+def _oracle_shard(arrays, n_events):
+    """Worker: the oracle, as it is, on one shard; returns its seconds."""
+    from oracle import oracle
+    from paper_1906_06242_gb300 import synth
+    b = synth.EventBatch(n_events=n_events, jet_offsets=arrays["off_jet"], mu_offsets=arrays["off_mu"],
+                         el_offsets=arrays["off_el"], cols=arrays, weight=arrays["weight"])
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run_chain(b, synth.CUTS, synth.HIST_SPECS, [0], per_event=False)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_all_cores(batch, n_sample):
+    """The same oracle on all host cores: the first n_sample events cut into
+    one contiguous shard per core, each run by the unchanged oracle in its
+    own spawned process (per-process histograms, as the paper's
+    multithreaded CPU backend keeps per-thread ones). Rate = events / the
+    slowest shard's compute time."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_1906_06242_gb300 import streaming
+    cores = os.cpu_count() or 1
+    n = min(n_sample, batch.n_events)
+    bounds = [n * r // cores for r in range(cores + 1)]
+    shards = [streaming.host_range(batch, bounds[r], bounds[r + 1]) for r in range(cores)]
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        times = list(ex.map(_oracle_shard, shards, [bounds[r + 1] - bounds[r] for r in range(cores)]))
+    worst = max(times)
+    return {"value": n / worst, "unit": "events/s", "cores": cores, "kind": "oracle, one process per core",
+            "sample": f"first {n} events of the {batch.n_events}-event workload in {cores} shards, "
+                      f"slowest shard {worst:.2f} s"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -318,6 +351,8 @@ def main():
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(batch, 4_000_000) if world == 1 else None
+    if world == 1 and not args.no_extra:
+        extra["cpu_oracle_all_cores"] = cpu_oracle_all_cores(batch, 4_000_000)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
