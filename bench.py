@@ -334,9 +334,37 @@ def main():
             e2e_step()
         b.record(stream)
         torch.cuda.synchronize()
+        serial_ms = a.elapsed_time(b) / k2
+        serial = {"value": world * batch.n_events / (serial_ms * 1e-3), "ms_per_step": serial_ms,
+                  "h2d_bytes_per_step": h2d, "form": "all columns copied, then one chain call"}
+        del dev_bufs, db2, out2, s2
+        # the headline form, through the streaming API: the copies of range i
+        # overlap the chain on range i-1 (ranges of about 1/8 of the columns)
+        from paper_1906_06242_gb300 import streaming
+        out3 = H.ChainOutputs(cfg, batch.n_events, per_event=False, sumw2=True)
+        sc = streaming.StreamedChain(batch, cfg, out3, batch_bytes=max(1 << 20, alg_bytes // 8))
+
+        def e2e_streamed():
+            out3.zero_()
+            sc.run(stream)
+            res_host[0].copy_(out3.counts, non_blocking=True)
+            res_host[1].copy_(out3.sumw, non_blocking=True)
+            res_host[2].copy_(out3.sumw2, non_blocking=True)
+
+        for _ in range(3):
+            e2e_streamed()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k2):
+            e2e_streamed()
+        b.record(stream)
+        torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / k2
-        e2e = {"value": world * batch.n_events / (e2e_ms * 1e-3), "unit": "events/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+        e2e = {"value": world * batch.n_events / (e2e_ms * 1e-3), "unit": "events/s",
+               "h2d_bytes_per_step": int(sc.h2d_bytes), "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "form": "streaming.StreamedChain: %d host ranges, copies overlapping the chain" % len(sc.ranges),
+               "serial": serial}
+        del sc, out3
 
     extra = {}
     if not args.no_extra and rank == 0:
