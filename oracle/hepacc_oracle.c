@@ -340,6 +340,39 @@ void oracle_fill_histogram(const void *x, int xt, const float *w, const uint8_t 
     }
 }
 
+/* Histogram over several variables (Section III notes that the fill
+ * extends to more dimensions). Axis d bins x[d][i] exactly as bin_of does
+ * (nbins[d] + 2 bins with under- and overflow); the cell of element i is
+ * the row-major index of (b_0, ..., b_{ndim-1}), axis 0 slowest. Elements
+ * with mask unset or a NaN on any axis are not filled. Accumulates. */
+void oracle_fill_histogram_nd(int ndim, const void *const *x, const int *xt, const float *const *edges,
+                              const int *nbins, const float *w, const uint8_t *mask, int64_t m,
+                              uint64_t *counts, double *sumw, double *sumw2)
+{
+    for (int64_t i = 0; i < m; i++) {
+        if (!on(mask, i))
+            continue;
+        int64_t cell = 0;
+        int skip = 0;
+        for (int d = 0; d < ndim; d++) {
+            int b = bin_of((double)get_f(x[d], xt[d], i), edges[d], nbins[d]);
+            if (b < 0) {
+                skip = 1;
+                break;
+            }
+            cell = cell * (nbins[d] + 2) + b;
+        }
+        if (skip)
+            continue;
+        double wi = w ? (double)w[i] : 1.0;
+        counts[cell] += 1;
+        if (sumw)
+            sumw[cell] += wi;
+        if (sumw2)
+            sumw2[cell] += wi * wi;
+    }
+}
+
 /* ---------------------------------------------------------------------------
  * Invariant masses (Section IV: pair and triplet candidates), FP64
  * ------------------------------------------------------------------------- */

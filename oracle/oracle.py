@@ -238,6 +238,30 @@ def fill_histogram(x, edges, weights=None, mask=None, counts=None, sumw=None, su
     return counts, sumw, sumw2
 
 
+def fill_histogram_nd(xs, edges, weights=None, mask=None, fmts=None):
+    """Histogram over len(xs) variables; returns counts, sumw, sumw2 shaped
+    (nbins_0 + 2, nbins_1 + 2, ...), axis 0 slowest in memory."""
+    k = len(xs)
+    fmts = fmts or [None] * k
+    edges = [np.ascontiguousarray(e, dtype=np.float32) for e in edges]
+    nbs = [len(e) - 1 for e in edges]
+    shape = tuple(nb + 2 for nb in nbs)
+    counts = np.zeros(shape, dtype=np.uint64)
+    sumw = np.zeros(shape, dtype=np.float64)
+    sumw2 = np.zeros(shape, dtype=np.float64)
+    xs = [np.ascontiguousarray(x) for x in xs]
+    xp = (ctypes.c_void_p * k)(*[x.ctypes.data for x in xs])
+    xt = (ctypes.c_int * k)(*[_code(x, f) for x, f in zip(xs, fmts)])
+    ep = (ctypes.c_void_p * k)(*[e.ctypes.data for e in edges])
+    nb = (ctypes.c_int * k)(*nbs)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    n = len(xs[0])
+    assert all(len(x) == n for x in xs)
+    lib().oracle_fill_histogram_nd(ctypes.c_int(k), xp, xt, ep, nb, _p(w), _p(_u8(mask)), _i64(n), _p(counts),
+                                   _p(sumw), _p(sumw2))
+    return counts, sumw, sumw2
+
+
 def pair_mass(pt, eta, phi, mass, offsets, ia, ib, mask_rows=None, fmt=None):
     n = len(offsets) - 1
     out = np.full(n, np.nan, dtype=np.float64)

@@ -38,6 +38,8 @@ MUTATIONS = [
     ("opposite sign ignores mask", "if (on(mask_in, j) && ", "if ("),
     ("lookup interpolates from the upper bin", "out[j] = contents[b] + prod;", "out[j] = contents[b + 1] - prod;"),
     ("lookup centre is the lower edge", "float cb = (edges[b - 1] + edges[b]) * 0.5f;", "float cb = edges[b - 1];"),
+    ("nd stride drops the flow bins", "cell = cell * (nbins[d] + 2) + b;", "cell = cell * (nbins[d] + 1) + b;"),
+    ("nd NaN goes to underflow", "skip = 1;\n                break;", "b = 0;"),
 ]
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

@@ -419,6 +419,71 @@ def test_histogram_edges_are_float32_of_binary64(orc):
     assert orc.bin_of(float(e[-1]), e) == 101         # upper edge is overflow
 
 
+def _numpy_nd(cols, edges, w):
+    """numpy.histogramdd with outer edges at +-1e300 added on every axis, so
+    that its cells are the under/overflow layout of the fill (the last numpy
+    bin is closed, which only matters at 1e300); infinities map to +-1e299."""
+    pts = np.stack([np.clip(c.astype(np.float64), -1e299, 1e299) for c in cols], axis=1)
+    bins = [np.concatenate([[-1e300], e.astype(np.float64), [1e300]]) for e in edges]
+    c, _ = np.histogramdd(pts, bins=bins)
+    sw, _ = np.histogramdd(pts, bins=bins, weights=w)
+    sw2, _ = np.histogramdd(pts, bins=bins, weights=w * w)
+    return c.astype(np.uint64), sw, sw2
+
+
+def test_histogram_nd_vs_numpy(orc):
+    """Three axes of different sizes and types (float32, int32, bf16), values
+    on edges, infinities, NaNs on each axis, a mask and weights."""
+    rng = np.random.default_rng(41)
+    n = 60_000
+    e0 = orc.hist_edges(-2.0, 2.0, 7)
+    e1 = np.array([-0.5, 0.5, 1.5, 2.5, 4.0, 7.0], np.float32)        # 5 bins
+    e2 = orc.hist_edges(0.0, 1.0, 3)
+    x0 = rng.normal(0, 1.5, n).astype(np.float32)
+    x1 = rng.poisson(2.5, n).astype(np.int32) - 1
+    x2f = rng.uniform(-0.2, 1.2, n).astype(np.float32)
+    x0[:8] = e0[[0, 1, 3, 7, 7, 6, 2, 5]]
+    x2f[:4] = e2[[0, 1, 2, 3]]
+    x0[8], x0[9] = np.inf, -np.inf
+    x0[10] = np.nan
+    x1[11] = 4                                   # an int on an edge
+    x2f[12] = np.nan
+    x2 = synth.to_half_bits(x2f, "bf16")
+    x2v = (x2.astype(np.uint32) << 16).view(np.float32)      # bf16 = the top half of a binary32
+    w = rng.normal(1, 0.2, n).astype(np.float32)
+    mask = (rng.random(n) < 0.9).astype(np.uint8)
+    counts, sumw, sumw2 = orc.fill_histogram_nd([x0, x1, x2], [e0, e1, e2], w, mask, fmts=[None, None, "bf16"])
+    assert counts.shape == (9, 7, 5)
+    ok = mask.astype(bool) & ~np.isnan(x0) & ~np.isnan(x2v)
+    rc, rw, rw2 = _numpy_nd([x0[ok], x1[ok], x2v[ok]], [e0, e1, e2], w[ok].astype(np.float64))
+    np.testing.assert_array_equal(counts, rc)
+    np.testing.assert_allclose(sumw, rw, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(sumw2, rw2, rtol=1e-12, atol=1e-12)
+    assert counts.sum() == ok.sum()
+    # the element on an exact int edge sits above it, the infinities at the ends
+    assert counts[:, 5, :].sum() == np.sum(ok & (x1 >= 4) & (x1 < 7))
+    assert counts[-1].sum() == np.sum(ok & (x0 >= e0[-1]))
+
+
+def test_histogram_nd_reduces_to_1d(orc):
+    """One axis is the one-dimensional fill; a second axis with a single
+    all-covering bin leaves the first axis' histogram unchanged."""
+    rng = np.random.default_rng(42)
+    x = rng.normal(0, 2, 20_000).astype(np.float32)
+    x[:3] = [np.nan, np.inf, -np.inf]
+    w = rng.normal(1, 0.1, len(x)).astype(np.float32)
+    e = orc.hist_edges(-3, 3, 11)
+    c1, w1, q1 = orc.fill_histogram(x, e, w)
+    cn, wn, qn = orc.fill_histogram_nd([x], [e], w)
+    np.testing.assert_array_equal(cn, c1)
+    np.testing.assert_array_equal(wn, w1)
+    y = np.zeros_like(x)
+    c2, w2, _ = orc.fill_histogram_nd([x, y], [e, np.array([-1, 1], np.float32)], w)
+    np.testing.assert_array_equal(c2[:, 1], c1)
+    assert c2[:, [0, 2]].sum() == 0
+    np.testing.assert_array_equal(w2[:, 1], w1)
+
+
 # ---------------------------------------------------------------------------
 # the chain on generated events
 # ---------------------------------------------------------------------------
