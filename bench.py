@@ -368,11 +368,13 @@ def main():
 
     extra = {}
     if not args.no_extra and rank == 0:
-        extra = secondary_forms(H, synth, batch, torch, stream)
-        extra["kernels"] = kernel_forms(H, batch, torch, stream)
-        extra.update(batched_forms(H, synth, torch, stream, args.batched_scale))
+        # the streamed dense form first: its host-to-device copies ran at a
+        # third of the link's rate when measured after the other forms
         if args.dense_events > 0:
             extra.update(dense_forms(H, synth, torch, stream, args.dense_events))
+        extra.update(secondary_forms(H, synth, batch, torch, stream))
+        extra["kernels"] = kernel_forms(H, batch, torch, stream)
+        extra.update(batched_forms(H, synth, torch, stream, args.batched_scale))
 
     if rank != 0:
         if dist:
@@ -484,6 +486,14 @@ def kernel_forms(H, batch, torch, stream):
     sumw = torch.zeros(102, dtype=torch.float64, device=dev)
     sumw2 = torch.zeros(102, dtype=torch.float64, device=dev)
     n_first = int((np.diff(batch.jet_offsets) > 0).sum())   # events with a first jet
+    q_mu = torch.from_numpy(batch.cols["mu_charge"]).to(dev)
+    mask_os = torch.empty(mm, dtype=torch.uint8, device=dev)
+    table = torch.linspace(0.9, 1.1, 102, device=dev)
+    corr = torch.empty(mj, dtype=torch.float32, device=dev)
+    edges_pt = torch.from_numpy(H.hist_edges(20.0, 500.0, 60)).to(dev)
+    edges_eta = torch.from_numpy(H.hist_edges(-2.5, 2.5, 50)).to(dev)
+    counts2 = torch.zeros((62, 52), dtype=torch.int64, device=dev)
+    sumw2d = torch.zeros((62, 52), dtype=torch.float64, device=dev)
     ops = {
         "sum_in_offsets": (lambda: H.hepacc_sum_in_offsets(C["jet_pt"], jo, out=out_f, stream=stream),
                            4 * mj + ob + 8 * n),
@@ -501,6 +511,17 @@ def kernel_forms(H, batch, torch, stream):
         "max_pt_trijet": (lambda: H.hepacc_max_pt_trijet(C["jet_pt"], C["jet_eta"], C["jet_phi"], C["jet_mass"], jo,
                                                          out_mass=out_f, out_pt=out_f2, out_idx3=idx3,
                                                          stream=stream), 16 * mj + ob + 20 * n),
+        "trijet_closest_mass": (lambda: H.hepacc_trijet_closest_mass(C["jet_pt"], C["jet_eta"], C["jet_phi"],
+                                                                     C["jet_mass"], jo, target=172.0, out_mass=out_f,
+                                                                     out_idx3=idx3, stream=stream),
+                                16 * mj + ob + 16 * n),
+        "select_opposite_sign": (lambda: H.hepacc_select_opposite_sign(q_mu, mo, mask_out=mask_os, stream=stream),
+                                 2 * mm + ob),
+        "get_bin_contents": (lambda: H.hepacc_get_bin_contents(C["jet_pt"], edges, table, interpolate=True, out=corr,
+                                                               stream=stream), 8 * mj),
+        "fill_histogram_nd": (lambda: H.hepacc_fill_histogram_nd([C["jet_pt"], C["jet_eta"]], [edges_pt, edges_eta],
+                                                                 counts=counts2, sumw=sumw2d, with_sumw2=False,
+                                                                 stream=stream), 8 * mj),
     }
     res = {}
     for name, (fn, nbytes) in ops.items():

@@ -198,6 +198,25 @@ hepacc_status hepacc_fill_histogram(const void *data, hepacc_dtype data_type, co
                                     const uint8_t *mask, int64_t n, const float *edges, int32_t nbins,
                                     uint64_t *counts, double *sumw, double *sumw2, hepacc_stream stream);
 
+/* Histogram over several variables (Section III: the fill extends to more
+ * dimensions). ndim in [1, HEPACC_MAX_HIST_DIMS]. Axis d bins data[d][j]
+ * (n elements of type data_types[d]: F32, F16, BF16, U8, I8 or I32) against
+ * the increasing binary32 edges[d][0..nbins[d]] exactly as
+ * hepacc_fill_histogram does, so axis d has nbins[d] + 2 bins with under-
+ * and overflow. The cell of element j is the row-major index of
+ * (b_0, ..., b_{ndim-1}), axis 0 slowest: ((b_0 (nbins[1]+2) + b_1)
+ * (nbins[2]+2) + b_2) ...; counts, sumw and sumw2 have prod_d (nbins[d]+2)
+ * <= 2^24 entries (sumw, sumw2 may be NULL), and counts[c] += 1,
+ * sumw[c] += w, sumw2[c] += w*w as in the one-dimensional fill. Elements with
+ * mask[j] unset or a NaN on any axis are not filled. data, data_types, edges
+ * and nbins are HOST arrays of ndim entries (data[d] and edges[d] are device
+ * pointers), read before the call returns. 1 <= nbins[d] <= 65536. */
+#define HEPACC_MAX_HIST_DIMS 4
+hepacc_status hepacc_fill_histogram_nd(int32_t ndim, const void *const *data, const hepacc_dtype *data_types,
+                                       const float *const *edges, const int32_t *nbins, const float *weights,
+                                       const uint8_t *mask, int64_t n, uint64_t *counts, double *sumw,
+                                       double *sumw2, hepacc_stream stream);
+
 /* Invariant mass of a pair of objects per event (Section IV: high-level
  * variables). For every event i with mask_rows[i] set: out[i] = mass of the
  * sum of the four-momenta of the objects at local indices idx_a[i] and

@@ -611,6 +611,127 @@ __global__ void __launch_bounds__(kBlock) k_hist_global(const T* x, const float*
     }
 }
 
+// Several variables: the axes' columns, edges and sizes (HEPACC_MAX_HIST_DIMS
+// at most), passed by value.
+struct HistAxes {
+    const void* x[HEPACC_MAX_HIST_DIMS];
+    const float* e[HEPACC_MAX_HIST_DIMS];
+    int dt[HEPACC_MAX_HIST_DIMS];
+    int nb[HEPACC_MAX_HIST_DIMS];
+    int ndim;
+};
+
+// Element j of a column whose type is known only at run time.
+__device__ __forceinline__ float ld_any(const void* p, int dt, int64_t j) {
+    switch (dt) {
+        case HEPACC_F32: return __ldg(static_cast<const float*>(p) + j);
+        case HEPACC_F16: return __half2float(static_cast<const __half*>(p)[j]);
+        case HEPACC_BF16: return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[j]);
+        case HEPACC_U8: return static_cast<float>(static_cast<const uint8_t*>(p)[j]);
+        case HEPACC_I8: return static_cast<float>(static_cast<const int8_t*>(p)[j]);
+        default: return static_cast<float>(__ldg(static_cast<const int32_t*>(p) + j));
+    }
+}
+
+// Row-major cell of element j over the axes (axis 0 slowest), -1 for a NaN
+// on any axis.
+__device__ __forceinline__ int64_t cell_of(const HistAxes& a, const float (&inv_w)[HEPACC_MAX_HIST_DIMS], int64_t j) {
+    int64_t at = 0;
+#pragma unroll
+    for (int d = 0; d < HEPACC_MAX_HIST_DIMS; ++d) {
+        if (d >= a.ndim) break;
+        const int b = find_bin(ld_any(a.x[d], a.dt[d], j), a.e[d], a.nb[d], inv_w[d]);
+        if (b < 0) return -1;
+        at = at * (a.nb[d] + 2) + b;
+    }
+    return at;
+}
+
+__device__ __forceinline__ void axis_widths(const HistAxes& a, float (&inv_w)[HEPACC_MAX_HIST_DIMS]) {
+#pragma unroll
+    for (int d = 0; d < HEPACC_MAX_HIST_DIMS; ++d) {
+        inv_w[d] = 0.0f;
+        if (d < a.ndim) {
+            const float span = __ldg(a.e[d] + a.nb[d]) - __ldg(a.e[d]);
+            inv_w[d] = span > 0.0f ? static_cast<float>(a.nb[d]) / span : 0.0f;
+        }
+    }
+}
+
+// fill_histogram_nd with a block-private histogram in shared memory (u32
+// counts, f64 sums; edges read through the read-only cache). Lanes of a warp
+// that hit the same cell are merged first, as in k_hist_smem.
+__global__ void __launch_bounds__(kBlock) k_hist_nd_smem(const __grid_constant__ HistAxes a, const float* w,
+                                                         const uint8_t* mask, int64_t n, int ncell,
+                                                         unsigned long long* counts, double* sumw, double* sumw2) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* s_w = reinterpret_cast<double*>(smem);
+    double* s_w2 = s_w + ncell;
+    double* s_lane = s_w2 + ncell;
+    unsigned int* s_c = reinterpret_cast<unsigned int*>(s_lane + blockDim.x);
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+        s_w[i] = 0.0;
+        s_w2[i] = 0.0;
+        s_c[i] = 0u;
+    }
+    float inv_w[HEPACC_MAX_HIST_DIMS];
+    axis_widths(a, inv_w);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double* my = s_lane + (threadIdx.x & ~31);
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += step) {
+        const int64_t j = base + lane;
+        int c = -1;
+        double ww = 0.0;
+        if (j < n && (!mask || mask[j])) {
+            c = static_cast<int>(cell_of(a, inv_w, j));
+            ww = w ? static_cast<double>(w[j]) : 1.0;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        my[lane] = ww;
+        __syncwarp();
+        if (c >= 0 && lane == __ffs(peers) - 1) {
+            double sw = 0.0, sw2 = 0.0;
+            for (unsigned m = peers; m; m &= m - 1) {
+                const double q = my[__ffs(m) - 1];
+                sw += q;
+                sw2 += q * q;
+            }
+            atomicAdd(&s_c[c], static_cast<unsigned>(__popc(peers)));
+            if (sumw) atomicAdd(&s_w[c], sw);
+            if (sumw2) atomicAdd(&s_w2[c], sw2);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+        if (s_c[i] == 0u) continue;
+        atomicAdd(&counts[i], static_cast<unsigned long long>(s_c[i]));
+        if (sumw) atomicAdd(&sumw[i], s_w[i]);
+        if (sumw2) atomicAdd(&sumw2[i], s_w2[i]);
+    }
+}
+
+// fill_histogram_nd straight into global memory (more cells than fit in
+// shared memory).
+__global__ void __launch_bounds__(kBlock) k_hist_nd_global(const __grid_constant__ HistAxes a, const float* w,
+                                                           const uint8_t* mask, int64_t n, unsigned long long* counts,
+                                                           double* sumw, double* sumw2) {
+    float inv_w[HEPACC_MAX_HIST_DIMS];
+    axis_widths(a, inv_w);
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask && !mask[j]) continue;
+        const int64_t c = cell_of(a, inv_w, j);
+        if (c < 0) continue;
+        const double ww = w ? static_cast<double>(w[j]) : 1.0;
+        atomicAdd(&counts[c], 1ull);
+        if (sumw) atomicAdd(&sumw[c], ww);
+        if (sumw2) atomicAdd(&sumw2[c], ww * ww);
+    }
+}
+
 template <typename OffT>
 __global__ void k_validate(const OffT* off, int64_t n, int64_t m, unsigned long long* first_bad) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -1088,6 +1209,48 @@ hepacc_status hepacc_fill_histogram(const void* data, hepacc_dtype dt, const flo
         HEPACC_CHECK_LAUNCH("fill_histogram launch");
         return HEPACC_OK;
     });
+}
+
+hepacc_status hepacc_fill_histogram_nd(int32_t ndim, const void* const* data, const hepacc_dtype* data_types,
+                                       const float* const* edges, const int32_t* nbins, const float* weights,
+                                       const uint8_t* mask, int64_t n, uint64_t* counts, double* sumw,
+                                       double* sumw2, hepacc_stream stream) {
+    HEPACC_CHECK(ndim >= 1 && ndim <= HEPACC_MAX_HIST_DIMS, "ndim must be in [1, %d]", HEPACC_MAX_HIST_DIMS);
+    HEPACC_CHECK(data && data_types && edges && nbins, "data, data_types, edges and nbins are required");
+    HEPACC_CHECK(n >= 0, "n < 0");
+    HistAxes a{};
+    a.ndim = ndim;
+    int64_t ncell = 1;
+    for (int d = 0; d < ndim; ++d) {
+        HEPACC_CHECK(nbins[d] >= 1 && nbins[d] <= 65536, "nbins[%d] must be in [1, 65536]", d);
+        switch (data_types[d]) {
+            case HEPACC_F32: case HEPACC_F16: case HEPACC_BF16: case HEPACC_U8: case HEPACC_I8: case HEPACC_I32:
+                break;
+            default: return fail(HEPACC_ERR_DTYPE, "unsupported data type on axis %d", d);
+        }
+        a.x[d] = data[d];
+        a.e[d] = edges[d];
+        a.dt[d] = static_cast<int>(data_types[d]);
+        a.nb[d] = nbins[d];
+        ncell *= nbins[d] + 2;
+        HEPACC_CHECK(ncell <= (int64_t(1) << 24), "more than 2^24 cells");
+        HEPACC_CHECK(n == 0 || (data[d] && edges[d]), "data[%d] and edges[%d] are required", d, d);
+    }
+    if (n == 0) return HEPACC_OK;
+    HEPACC_CHECK(counts, "counts is required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+    if (ncell <= 4096) {
+        const size_t smem = static_cast<size_t>(ncell) * (8 + 8 + 4) + kBlock * 8;
+        int grid = 0;
+        hepacc_status st = tile_grid(k_hist_nd_smem, smem, (n + 31) / 32, &grid);
+        if (st != HEPACC_OK) return st;
+        k_hist_nd_smem<<<grid, kBlock, smem, s>>>(a, weights, mask, n, static_cast<int>(ncell), c, sumw, sumw2);
+    } else {
+        k_hist_nd_global<<<flat_grid(n), kBlock, 0, s>>>(a, weights, mask, n, c, sumw, sumw2);
+    }
+    HEPACC_CHECK_LAUNCH("fill_histogram_nd launch");
+    return HEPACC_OK;
 }
 
 hepacc_status hepacc_selftest_wait_timeout(int64_t limit_cycles, hepacc_stream stream) {

@@ -66,7 +66,7 @@ def load(build_if_missing: bool = True):
                  "hepacc_run_chain", "hepacc_validate_offsets", "hepacc_device_error",
                  "hepacc_selftest_wait_timeout", "hepacc_plan_create", "hepacc_plan_run",
                  "hepacc_plan_describe", "hepacc_trijet_closest_mass", "hepacc_select_opposite_sign",
-                 "hepacc_get_bin_contents"):
+                 "hepacc_get_bin_contents", "hepacc_fill_histogram_nd"):
         getattr(L, name).restype = ctypes.c_int
     L.hepacc_plan_destroy.restype = None
     L.hepacc_plan_destroy.argtypes = [ctypes.c_void_p]
@@ -237,6 +237,33 @@ def hepacc_fill_histogram(data, edges, weights=None, mask=None, counts=None, sum
     _check(load().hepacc_fill_histogram(_ptr(data), _code(data), _ptr(weights), _ptr(mask), _i64(data.numel()),
                                         _ptr(edges), _i32(nb), _ptr(counts), _ptr(sumw), _ptr(sumw2),
                                         _stream(stream)))
+    return counts, sumw, sumw2
+
+
+def hepacc_fill_histogram_nd(data, edges, weights=None, mask=None, counts=None, sumw=None, sumw2=None,
+                             with_sumw2=True, stream=None):
+    """Histogram over len(data) variables; the outputs are shaped
+    (nbins_0 + 2, nbins_1 + 2, ...), axis 0 slowest."""
+    k = len(data)
+    if k != len(edges):
+        raise ValueError("one edges tensor per axis")
+    shape = tuple(e.numel() + 1 for e in edges)
+    dev = data[0].device
+    if counts is None:
+        counts = torch.zeros(shape, dtype=torch.int64, device=dev)
+    if sumw is None:
+        sumw = torch.zeros(shape, dtype=torch.float64, device=dev)
+    if sumw2 is None and with_sumw2:
+        sumw2 = torch.zeros(shape, dtype=torch.float64, device=dev)
+    n = data[0].numel()
+    if any(x.numel() != n for x in data):
+        raise ValueError("all axes need the same number of elements")
+    ptrs = (ctypes.c_void_p * k)(*[_ptr(x) for x in data])
+    types = (ctypes.c_int * k)(*[_code(x) for x in data])
+    eptrs = (ctypes.c_void_p * k)(*[_ptr(e) for e in edges])
+    nbs = (ctypes.c_int32 * k)(*[e.numel() - 1 for e in edges])
+    _check(load().hepacc_fill_histogram_nd(_i32(k), ptrs, types, eptrs, nbs, _ptr(weights), _ptr(mask),
+                                           _i64(n), _ptr(counts), _ptr(sumw), _ptr(sumw2), _stream(stream)))
     return counts, sumw, sumw2
 
 

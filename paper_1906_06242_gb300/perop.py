@@ -141,6 +141,19 @@ def run_chain_per_op(b: H.DeviceBatch, cfg: H.ChainConfig, out: H.ChainOutputs, 
     return out
 
 
+def dimuon_mass(pt, eta, phi, mass, charge, offsets, mask_in=None, stream=None):
+    """Dimuon candidate per event (Section III, select_opposite_sign_muons,
+    then a pair mass): the first opposite-charge pair among the muons with
+    mask_in set, its two local indices (get_in_offsets with n = 0 and 1 over
+    the pair mask) and its invariant mass; NaN and -1, -1 without a pair.
+    Returns (mass, idx_a, idx_b, pair_mask)."""
+    pair = H.hepacc_select_opposite_sign(charge, offsets, mask_in=mask_in, stream=stream)
+    _, ia = H.hepacc_get_in_offsets(pt, offsets, nth=0, mask_content=pair, stream=stream)
+    _, ib = H.hepacc_get_in_offsets(pt, offsets, nth=1, mask_content=pair, stream=stream)
+    m = H.hepacc_pair_mass(pt, eta, phi, mass, offsets, ia, ib, stream=stream)
+    return m, ia, ib, pair
+
+
 def _scratch_idx(ws):
     if not hasattr(ws, "_idx_scratch"):
         ws._idx_scratch = torch.empty_like(ws.lead_idx)

@@ -10,7 +10,8 @@ variation, hepacc_run_chain. ``batched``: the 12-sample set with 21 jet-pt
 variations as one plan (no autotuning, no graph, so that every launch is a
 plain kernel launch); ``--placement`` picks the histogram placement.
 ``op``: one per-operation kernel on the jets of the plain sample (sum, max,
-get, select, scale, mask_deltar, fill_histogram, max_pt_trijet). One untimed
+get, select, scale, mask_deltar, fill_histogram, max_pt_trijet,
+trijet_closest_mass, fill_histogram_nd over jet pt and eta). One untimed
 run, then ``--runs`` timed runs; prints the mean device time per run.
 """
 from __future__ import annotations
@@ -53,6 +54,9 @@ def main(argv=None):
         edges = torch.from_numpy(H.hist_edges(20.0, 500.0, 100)).cuda()
         hc = torch.zeros(102, dtype=torch.int64, device="cuda")
         hw = torch.zeros(102, dtype=torch.float64, device="cuda")
+        edges_eta = torch.from_numpy(H.hist_edges(-2.5, 2.5, 30)).cuda()
+        hc2 = torch.zeros((102, 32), dtype=torch.int64, device="cuda")
+        hw2 = torch.zeros((102, 32), dtype=torch.float64, device="cuda")
         ops = {
             "sum_in_offsets": lambda: H.hepacc_sum_in_offsets(C["jet_pt"], jo, out=f),
             "max_in_offsets": lambda: H.hepacc_max_in_offsets(C["jet_pt"], jo, out=f, arg=i),
@@ -65,6 +69,10 @@ def main(argv=None):
                                                               with_sumw2=False),
             "max_pt_trijet": lambda: H.hepacc_max_pt_trijet(C["jet_pt"], C["jet_eta"], C["jet_phi"], C["jet_mass"], jo,
                                                             out_mass=f, out_idx3=i3),
+            "trijet_closest_mass": lambda: H.hepacc_trijet_closest_mass(C["jet_pt"], C["jet_eta"], C["jet_phi"],
+                                                                        C["jet_mass"], jo, out_mass=f, out_idx3=i3),
+            "fill_histogram_nd": lambda: H.hepacc_fill_histogram_nd([C["jet_pt"], C["jet_eta"]], [edges, edges_eta],
+                                                                    counts=hc2, sumw=hw2, with_sumw2=False),
         }
         run = ops[a.op]
     elif a.workload == "plain":

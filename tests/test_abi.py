@@ -99,3 +99,26 @@ def test_plan_host_side_errors_without_gpu(lib):
     assert create(batch(), no_counts) == 1
     assert plan.value is None
     lib.hepacc_plan_destroy(None)
+
+
+def test_histogram_nd_host_side_errors_without_gpu(lib):
+    lib.hepacc_last_error.restype = ctypes.c_char_p
+    dummy = 16
+
+    def call(ndim, types, nbins, n=10, counts=dummy):
+        k = max(1, len(types))
+        data = (ctypes.c_void_p * k)(*([dummy] * k))
+        edges = (ctypes.c_void_p * k)(*([dummy] * k))
+        tt = (ctypes.c_int * k)(*(types or [0]))
+        nb = (ctypes.c_int32 * k)(*(nbins or [1]))
+        return lib.hepacc_fill_histogram_nd(ctypes.c_int32(ndim), data, tt, edges, nb, None, None,
+                                            ctypes.c_int64(n), ctypes.c_void_p(counts), None, None, None)
+
+    assert call(0, [0], [4]) == 1                          # no axis
+    assert call(5, [0] * 5, [4] * 5) == 1                  # more than HEPACC_MAX_HIST_DIMS
+    assert call(2, [0, 6], [4, 4]) == 2                    # int64 data is not a histogram axis
+    assert call(2, [0, 0], [4, 0]) == 1                    # an axis without bins
+    assert call(2, [0, 0], [4095, 4095]) == 1 and b"2^24" in lib.hepacc_last_error()   # 4097^2 cells
+    assert call(2, [0, 0], [4, 4], n=-1) == 1
+    assert call(2, [0, 0], [4, 4], counts=None) == 1       # counts required
+    assert call(2, [0, 0], [4, 4], n=0, counts=None) == 0  # empty input is a no-op

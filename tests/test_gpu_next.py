@@ -1,6 +1,7 @@
 """GPU parity of the next-row kernels against the oracle, through the C ABI:
 the top candidate closest to the top mass (Section IV), the opposite-sign
-pair selection and the histogram lookup (Section III)."""
+pair selection with its dimuon mass histogram, the histogram lookup and the
+histogram over several variables (Section III)."""
 import numpy as np
 import pytest
 import torch
@@ -129,3 +130,104 @@ def test_get_bin_contents_one_bin_and_empty(H, orc):
         np.testing.assert_array_equal(got, want)
     empty = torch.empty(0, dtype=torch.float32, device="cuda")
     assert H.hepacc_get_bin_contents(empty, dev(edges), dev(contents)).numel() == 0
+
+
+def _nd_case(case, n, orc):
+    """(columns, fmts, edges) of one multi-variable histogram case."""
+    rng = np.random.default_rng({"3d_smem": 31, "2d_global": 32, "4d_smem": 33}[case])
+    if case == "3d_smem":
+        x0 = rng.normal(0, 1.5, n).astype(np.float32)
+        x1 = (rng.poisson(2.5, n) - 1).astype(np.int32)
+        x2 = synth.to_half_bits(rng.uniform(-0.2, 1.2, n).astype(np.float32), "bf16")
+        edges = [orc.hist_edges(-2.0, 2.0, 7), np.array([-0.5, 0.5, 1.5, 2.5, 4.0, 7.0], np.float32),
+                 orc.hist_edges(0.0, 1.0, 3)]
+        cols, fmts = [x0, x1, x2], [None, None, "bf16"]
+        x0[:8] = edges[0][[0, 1, 3, 7, 7, 6, 2, 5]]
+        x0[8], x0[9], x0[10] = np.inf, -np.inf, np.nan
+    elif case == "2d_global":                      # 102 x 102 cells: the global-memory kernel
+        x0 = rng.normal(0, 1.2, n).astype(np.float32)
+        x1 = rng.uniform(-0.1, 1.1, n).astype(np.float32)
+        x1[::97] = np.nan
+        e1 = np.sort(rng.uniform(0, 1, 101)).astype(np.float32)      # uneven bins
+        edges = [orc.hist_edges(-3.0, 3.0, 100), e1]
+        x1[:101] = e1
+        cols, fmts = [x0, x1], [None, None]
+    else:                                          # four axes, four types
+        x0 = synth.to_half_bits(rng.normal(0, 1, n).astype(np.float32), "f16")
+        x1 = rng.integers(0, 6, n).astype(np.uint8)
+        x2 = rng.integers(-3, 3, n).astype(np.int8)
+        x3 = rng.exponential(1.0, n).astype(np.float32)
+        edges = [orc.hist_edges(-1.5, 1.5, 3), np.array([0.5, 1.5, 2.5, 3.5, 4.5], np.float32),
+                 np.array([-1.0, 0.0, 1.0], np.float32), orc.hist_edges(0.0, 2.5, 5)]
+        cols, fmts = [x0, x1, x2, x3], ["f16", None, None, None]
+    return cols, fmts, edges
+
+
+@pytest.mark.parametrize("case", ["3d_smem", "2d_global", "4d_smem"])
+def test_fill_histogram_nd(H, orc, case):
+    n = 300_007
+    cols, fmts, edges = _nd_case(case, n, orc)
+    rng = np.random.default_rng(34)
+    w = rng.normal(1, 0.2, n).astype(np.float32)
+    mask = (rng.random(n) < 0.9).astype(np.uint8)
+    oc, ow, ow2 = orc.fill_histogram_nd(cols, edges, w, mask, fmts=fmts)
+    gc, gw, gw2 = H.hepacc_fill_histogram_nd([dev(c, f) for c, f in zip(cols, fmts)], [dev(e) for e in edges],
+                                             weights=dev(w), mask=dev(mask))
+    torch.cuda.synchronize()
+    assert tuple(gc.shape) == oc.shape
+    np.testing.assert_array_equal(gc.cpu().numpy().astype(np.uint64), oc)
+    np.testing.assert_allclose(gw.cpu().numpy(), ow, rtol=1e-9, atol=1e-9)      # binary64, any order
+    np.testing.assert_allclose(gw2.cpu().numpy(), ow2, rtol=1e-9, atol=1e-9)
+    # no weights, no mask: plain counts; the second call accumulates
+    oc1, _, _ = orc.fill_histogram_nd(cols, edges, fmts=fmts)
+    args = ([dev(c, f) for c, f in zip(cols, fmts)], [dev(e) for e in edges])
+    gc1, gw1, _ = H.hepacc_fill_histogram_nd(*args)
+    H.hepacc_fill_histogram_nd(*args, counts=gc1, sumw=gw1, with_sumw2=False)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(gc1.cpu().numpy().astype(np.uint64), 2 * oc1)
+    np.testing.assert_array_equal(gw1.cpu().numpy(), 2 * oc1.astype(np.float64))
+    assert H.device_error() == 0
+
+
+def test_fill_histogram_nd_empty(H):
+    e = torch.tensor([0.0, 1.0], device="cuda")
+    x = torch.empty(0, device="cuda")
+    c, w, _ = H.hepacc_fill_histogram_nd([x, x], [e, e])
+    torch.cuda.synchronize()
+    assert c.shape == (3, 3) and int(c.sum()) == 0 and float(w.sum()) == 0.0
+
+
+def test_dimuon_mass_histogram(H, orc):
+    """Opposite-sign muon pair, its mass and its weighted histogram, composed
+    from the per-operation kernels, against the same steps in the oracle."""
+    from paper_1906_06242_gb300 import perop
+    b = synth.generate(80_001, 23, lam_mu=2.5, offset_dtype=np.int64)
+    c, off = b.cols, b.mu_offsets
+    rng = np.random.default_rng(6)
+    mask_in = (rng.random(len(c["mu_pt"])) < 0.85).astype(np.uint8)
+    edges = orc.hist_edges(0.0, 300.0, 60)
+    pair_o = np.zeros(len(c["mu_pt"]), np.uint8)
+    orc.select_opposite_sign(c["mu_charge"], off, mask_in=mask_in, out=pair_o)
+    _, ia_o = orc.get_in_offsets(c["mu_pt"], off, 0, mask_content=pair_o)
+    _, ib_o = orc.get_in_offsets(c["mu_pt"], off, 1, mask_content=pair_o)
+    m_o = orc.pair_mass(c["mu_pt"], c["mu_eta"], c["mu_phi"], c["mu_mass"], off, ia_o, ib_o)
+    hc_o, hw_o, _ = orc.fill_histogram(m_o.astype(np.float32), edges, b.weight)
+    m, ia, ib, pair = perop.dimuon_mass(dev(c["mu_pt"]), dev(c["mu_eta"]), dev(c["mu_phi"]), dev(c["mu_mass"]),
+                                        dev(c["mu_charge"]), dev(off), mask_in=dev(mask_in))
+    hc, hw, _ = H.hepacc_fill_histogram(m, dev(edges), weights=dev(b.weight))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(pair.cpu().numpy(), pair_o)
+    np.testing.assert_array_equal(ia.cpu().numpy(), ia_o)
+    np.testing.assert_array_equal(ib.cpu().numpy(), ib_o)
+    m = m.cpu().numpy()
+    have = ~np.isnan(m_o)
+    assert (np.isnan(m) == ~have).all() and have.sum() > 1000
+    assert (np.abs(m[have] - m_o[have]) / m_o[have]).max() < 1e-5
+    # binned from binary32 masses: only events within the mass tolerance of an edge may move
+    e64 = edges.astype(np.float64)
+    near = np.abs(m_o[have, None] - e64[None, :]).min(axis=1) <= 2e-5 * m_o[have]
+    hc = hc.cpu().numpy().astype(np.int64)
+    assert hc.sum() == hc_o.sum() == have.sum()
+    assert np.abs(hc - hc_o.astype(np.int64)).sum() <= 2 * near.sum()
+    if near.sum() == 0:
+        np.testing.assert_allclose(hw.cpu().numpy(), hw_o, rtol=1e-9, atol=1e-9)
