@@ -531,6 +531,149 @@ __global__ void __launch_bounds__(kBlock) k_scale(const T* x, int64_t n, float s
         out[j] = __fmul_rn(ldf(x, j), s);
 }
 
+// ---------------------------------------------------------------------------
+// Exact weighted sums with integer arithmetic. A finite binary32 value is
+// m 2^(e-150) (e its biased exponent, m its 24-bit significand; e = 1 and no
+// implicit bit for subnormals), i.e. x 2^(8 (e >> 3) - 150) with the integer
+// x = m << (e & 7) < 2^31. The accumulator of exponent group e >> 3 adds the
+// low 16 bits and the high 15 bits of +-x in two int32 words (shared-memory
+// int32 atomics are fast, int64 ones are not); a launch gives each block at
+// most 2^15 elements, so neither word can overflow and the block's sums are
+// exact until each group is converted to binary64 once, at the end. The
+// binary64 pipe (narrow on this part) does no per-element work. w^2 enters
+// exactly as p + q with p = fl(w w) and q = w w - p from a fused
+// multiply-add. Weights outside [2^-50, 2^63) in magnitude (where p or q
+// could leave the binary32 range), infinities and NaNs go to the global
+// binary64 sums directly.
+// ---------------------------------------------------------------------------
+constexpr int kWG = 15;      // groups of w: |w| in [2^-50, 2^63) has e in [77, 189], groups 9..23
+constexpr int kWG0 = 9;
+constexpr int kW2G = 32;     // groups of p and q: every finite binary32 value
+// words per bin: odd, so that lanes on different bins and the same group
+// fall in different shared-memory banks
+constexpr int kWS = 2 * kWG + 1;
+constexpr int kW2S = 2 * kW2G + 1;
+constexpr int64_t kExactPerBlock = int64_t(1) << 15;
+constexpr size_t kExactSmemMax = 96 * 1024;   // two blocks per SM
+
+__device__ __forceinline__ bool exact_weight(float w) {
+    const uint32_t e = (__float_as_uint(w) >> 23) & 0xffu;
+    return w == 0.0f || (e >= 77u && e <= 189u);
+}
+
+// adds the finite binary32 value v to the int32 word pairs acc (group 0 of
+// acc is exponent group g0)
+__device__ __forceinline__ void exact_put(float v, int* acc, int g0) {
+    const uint32_t bits = __float_as_uint(v);
+    uint32_t e = (bits >> 23) & 0xffu;
+    uint32_t m = bits & 0x7fffffu;
+    if (e) m |= 0x800000u;
+    else e = 1u;
+    const uint32_t x = m << (e & 7u);
+    int lo = static_cast<int>(x & 0xffffu), hi = static_cast<int>(x >> 16);
+    if (bits >> 31) {
+        lo = -lo;
+        hi = -hi;
+    }
+    int* a = acc + 2 * (static_cast<int>(e >> 3) - g0);
+    atomicAdd(a, lo);
+    atomicAdd(a + 1, hi);
+}
+
+// Adds weight w of one element of bin/cell c to the block's accumulators (or
+// to the global sums when w is outside the exact range).
+__device__ __forceinline__ void exact_add(int c, float w, int* s_w, int* s_w2, double* sumw, double* sumw2) {
+    if (!exact_weight(w)) {
+        const double wd = static_cast<double>(w);
+        if (sumw) atomicAdd(&sumw[c], wd);
+        if (sumw2) atomicAdd(&sumw2[c], wd * wd);
+        return;
+    }
+    if (w == 0.0f) return;
+    if (s_w) exact_put(w, s_w + kWS * c, kWG0);
+    if (s_w2) {
+        const float p = __fmul_rn(w, w);
+        const float q = __fmaf_rn(w, w, -p);
+        exact_put(p, s_w2 + kW2S * c, 0);
+        if (q != 0.0f) exact_put(q, s_w2 + kW2S * c, 0);
+    }
+}
+
+// binary64 value of one bin's groups (first group g0, ng groups)
+__device__ __forceinline__ double exact_value(const int* acc, int g0, int ng) {
+    double s = 0.0;
+    for (int g = 0; g < ng; ++g) {
+        const long long a = static_cast<long long>(acc[2 * g]) + (static_cast<long long>(acc[2 * g + 1]) << 16);
+        if (a == 0) continue;
+        const double unit = __longlong_as_double(static_cast<long long>(1023 + 8 * (g0 + g) - 150) << 52);
+        s += __ll2double_rn(a) * unit;
+    }
+    return s;
+}
+
+// Shared memory of the exact-sum kernels: int32 word pairs of w and w^2 per
+// bin and group (kWS, kW2S words per bin), then u32 counts (then the edges for the one-variable kernel).
+inline size_t exact_smem(int64_t nbin, bool with_w, bool with_w2) {
+    return static_cast<size_t>(nbin) * ((with_w ? kWS * 4 : 0) + (with_w2 ? kW2S * 4 : 0) + 4);
+}
+
+__device__ __forceinline__ void exact_layout(unsigned char* smem, int nbin, bool with_w, bool with_w2, int*& s_w,
+                                             int*& s_w2, unsigned int*& s_c) {
+    int* p = reinterpret_cast<int*>(smem);
+    s_w2 = with_w2 ? p : nullptr;
+    p += with_w2 ? static_cast<size_t>(nbin) * kW2S : 0;
+    s_w = with_w ? p : nullptr;
+    p += with_w ? static_cast<size_t>(nbin) * kWS : 0;
+    s_c = reinterpret_cast<unsigned int*>(p);
+}
+
+__device__ __forceinline__ void exact_zero(int nbin, int* s_w, int* s_w2, unsigned int* s_c) {
+    for (int i = threadIdx.x; i < nbin; i += blockDim.x) s_c[i] = 0u;
+    if (s_w)
+        for (int i = threadIdx.x; i < nbin * kWS; i += blockDim.x) s_w[i] = 0;
+    if (s_w2)
+        for (int i = threadIdx.x; i < nbin * kW2S; i += blockDim.x) s_w2[i] = 0;
+}
+
+__device__ __forceinline__ void exact_merge(int nbin, const int* s_w, const int* s_w2, const unsigned int* s_c,
+                                            unsigned long long* counts, double* sumw, double* sumw2) {
+    for (int i = threadIdx.x; i < nbin; i += blockDim.x) {
+        if (s_c[i] == 0u) continue;
+        atomicAdd(&counts[i], static_cast<unsigned long long>(s_c[i]));
+        if (s_w) atomicAdd(&sumw[i], exact_value(s_w + kWS * i, kWG0, kWG));
+        if (s_w2) atomicAdd(&sumw2[i], exact_value(s_w2 + kW2S * i, 0, kW2G));
+    }
+}
+
+// fill_histogram with a block-private histogram in shared memory and exact
+// integer weighted sums (see above); lanes add their own element.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_hist_exact(const T* x, const float* w, const uint8_t* mask, int64_t n,
+                                                       const float* edges, int nb, unsigned long long* counts,
+                                                       double* sumw, double* sumw2) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nbin = nb + 2;
+    int *s_w, *s_w2;
+    unsigned int* s_c;
+    exact_layout(smem, nbin, sumw != nullptr, sumw2 != nullptr, s_w, s_w2, s_c);
+    float* s_e = reinterpret_cast<float*>(s_c + nbin);
+    exact_zero(nbin, s_w, s_w2, s_c);
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x) s_e[i] = edges[i];
+    __syncthreads();
+    const float span = s_e[nb] - s_e[0];
+    const float inv_width = span > 0.0f ? static_cast<float>(nb) / span : 0.0f;
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask && !mask[j]) continue;
+        const int b = find_bin(ldf(x, j), s_e, nb, inv_width);
+        if (b < 0) continue;
+        atomicAdd(&s_c[b], 1u);
+        exact_add(b, w ? w[j] : 1.0f, s_w, s_w2, sumw, sumw2);
+    }
+    __syncthreads();
+    exact_merge(nbin, s_w, s_w2, s_c, counts, sumw, sumw2);
+}
+
 // fill_histogram with a block-private copy of the histogram in shared memory:
 // edges, u32 counts, f64 sums. Lanes that hit the same bin are merged first
 // (__match_any_sync) so one lane per bin does the shared-memory atomics; the
@@ -730,6 +873,30 @@ __global__ void __launch_bounds__(kBlock) k_hist_nd_global(const __grid_constant
         if (sumw) atomicAdd(&sumw[c], ww);
         if (sumw2) atomicAdd(&sumw2[c], ww * ww);
     }
+}
+
+// fill_histogram_nd with a block-private histogram and exact integer sums.
+__global__ void __launch_bounds__(kBlock) k_hist_nd_exact(const __grid_constant__ HistAxes a, const float* w,
+                                                          const uint8_t* mask, int64_t n, int ncell,
+                                                          unsigned long long* counts, double* sumw, double* sumw2) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *s_w, *s_w2;
+    unsigned int* s_c;
+    exact_layout(smem, ncell, sumw != nullptr, sumw2 != nullptr, s_w, s_w2, s_c);
+    exact_zero(ncell, s_w, s_w2, s_c);
+    float inv_w[HEPACC_MAX_HIST_DIMS];
+    axis_widths(a, inv_w);
+    __syncthreads();
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (mask && !mask[j]) continue;
+        const int c = static_cast<int>(cell_of(a, inv_w, j));
+        if (c < 0) continue;
+        atomicAdd(&s_c[c], 1u);
+        exact_add(c, w ? w[j] : 1.0f, s_w, s_w2, sumw, sumw2);
+    }
+    __syncthreads();
+    exact_merge(ncell, s_w, s_w2, s_c, counts, sumw, sumw2);
 }
 
 template <typename OffT>
@@ -1195,6 +1362,22 @@ hepacc_status hepacc_fill_histogram(const void* data, hepacc_dtype dt, const flo
     return with_value_type(dt, [&](auto t) -> hepacc_status {
         using T = typename decltype(t)::type;
         const int nbin = nbins + 2;
+        const size_t ex_smem = exact_smem(nbin, sumw != nullptr, sumw2 != nullptr) + static_cast<size_t>(nbins + 1) * 4;
+        if (ex_smem <= kExactSmemMax) {
+            int grid = 0;
+            hepacc_status st = tile_grid(k_hist_exact<T>, ex_smem, (n + 31) / 32, &grid);
+            if (st != HEPACC_OK) return st;
+            // no block adds more than kExactPerBlock elements in one launch
+            const int64_t chunk = static_cast<int64_t>(grid) * kExactPerBlock;
+            const T* xt = static_cast<const T*>(data);
+            for (int64_t off = 0; off < n; off += chunk) {
+                k_hist_exact<T><<<grid, kBlock, ex_smem, s>>>(xt + off, weights ? weights + off : nullptr,
+                                                              mask ? mask + off : nullptr, std::min(chunk, n - off),
+                                                              edges, nbins, c, sumw, sumw2);
+                HEPACC_CHECK_LAUNCH("fill_histogram launch");
+            }
+            return HEPACC_OK;
+        }
         const size_t smem = static_cast<size_t>(nbin) * (8 + 8 + 4) + static_cast<size_t>(nbins + 1) * 4 + kBlock * 8;
         if (nbin <= 4096) {
             int grid = 0;
@@ -1240,6 +1423,23 @@ hepacc_status hepacc_fill_histogram_nd(int32_t ndim, const void* const* data, co
     HEPACC_CHECK(counts, "counts is required");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+    const size_t ex_smem = exact_smem(ncell, sumw != nullptr, sumw2 != nullptr);
+    if (ex_smem <= kExactSmemMax) {
+        int grid = 0;
+        hepacc_status st = tile_grid(k_hist_nd_exact, ex_smem, (n + 31) / 32, &grid);
+        if (st != HEPACC_OK) return st;
+        const int64_t chunk = static_cast<int64_t>(grid) * kExactPerBlock;
+        for (int64_t off = 0; off < n; off += chunk) {
+            HistAxes ac = a;
+            for (int d = 0; d < ndim; ++d)
+                ac.x[d] = static_cast<const unsigned char*>(a.x[d]) + off * dtype_size(data_types[d]);
+            k_hist_nd_exact<<<grid, kBlock, ex_smem, s>>>(ac, weights ? weights + off : nullptr,
+                                                          mask ? mask + off : nullptr, std::min(chunk, n - off),
+                                                          static_cast<int>(ncell), c, sumw, sumw2);
+            HEPACC_CHECK_LAUNCH("fill_histogram_nd launch");
+        }
+        return HEPACC_OK;
+    }
     if (ncell <= 4096) {
         const size_t smem = static_cast<size_t>(ncell) * (8 + 8 + 4) + kBlock * 8;
         int grid = 0;

@@ -215,8 +215,10 @@ def test_mask_deltar(H, orc, fmt, od):
     np.testing.assert_array_equal(host(d), want)
 
 
-@pytest.mark.parametrize("nbins,uniform,dt", [(100, True, "f32"), (37, False, "f32"), (5000, True, "f32"),
-                                              (100, True, "bf16"), (64, True, "i32")])
+# 100, 37, 64 bins: exact integer sums; 1000 bins: binary64 shared-memory
+# sums; 5000 bins: global memory
+@pytest.mark.parametrize("nbins,uniform,dt", [(100, True, "f32"), (37, False, "f32"), (1000, True, "f32"),
+                                              (5000, True, "f32"), (100, True, "bf16"), (64, True, "i32")])
 def test_fill_histogram(H, orc, nbins, uniform, dt):
     rng = np.random.default_rng(13)
     n = 300007
@@ -245,6 +247,43 @@ def test_fill_histogram(H, orc, nbins, uniform, dt):
     gc2, gs2_, _ = H.hepacc_fill_histogram(dev(xh, ofmt), d_e, counts=gc.clone(), sumw=gs.clone(), with_sumw2=False)
     wc2, _, _ = orc.fill_histogram(xh, edges, None, None, fmt=ofmt)
     np.testing.assert_array_equal(host(gc2).astype(np.uint64), wc + wc2)
+
+
+def test_fill_histogram_weight_edge_cases(H, orc):
+    """Weights the integer sums take exactly (normal, zero, negative) and the
+    ones they hand to binary64 (subnormal, below 2^-50, at or above 2^63,
+    infinite, NaN), each in a bin of its own next to ordinary weights."""
+    rng = np.random.default_rng(17)
+    n = 200_003
+    edges = orc.hist_edges(0.0, 10.0, 10)
+    x = rng.uniform(0.0, 10.0, n).astype(np.float32)
+    w = rng.normal(1.0, 0.5, n).astype(np.float32)
+    special = {0.5: 0.0, 1.5: -0.0, 2.5: 1e-40, 3.5: 3e-16, 4.5: 2.0 ** 63, 5.5: 1e25, 6.5: np.inf,
+               7.5: np.nan, 8.5: -3.0e18, 9.5: 2.0 ** -50}
+    for k, (xv, wv) in enumerate(special.items()):
+        x[k * 7:(k + 1) * 7] = xv
+        w[k * 7:(k + 1) * 7] = wv
+    wc, ws, ws2 = orc.fill_histogram(x, edges, w)
+    gc, gs, gs2 = H.hepacc_fill_histogram(dev(x), dev(edges), weights=dev(w))
+    np.testing.assert_array_equal(host(gc).astype(np.uint64), wc)
+    np.testing.assert_allclose(host(gs), ws, rtol=1e-9, atol=1e-9, equal_nan=True)
+    np.testing.assert_allclose(host(gs2), ws2, rtol=1e-9, atol=1e-9, equal_nan=True)
+
+
+def test_fill_histogram_sums_are_exact(H):
+    """One weight repeated m times in one bin: the integer sums give m w
+    exactly (m w fits in binary64); m w^2 is exact per block, then rounded
+    once per block and added over the blocks in binary64 (a few hundred
+    roundings: relative error below 1e-12)."""
+    m = 3_000_017
+    x = torch.full((m,), 0.5, device="cuda")
+    edges = torch.tensor([0.0, 1.0], device="cuda")
+    for wv in (0.1, -7.3e-9, 1234.567):
+        w = torch.full((m,), wv, dtype=torch.float32, device="cuda")
+        c, s, s2 = H.hepacc_fill_histogram(x, edges, weights=w)
+        w32 = float(np.float32(wv))
+        assert int(c[1]) == m and float(s[1]) == m * w32
+        assert float(s2[1]) == pytest.approx(m * w32 * w32, rel=1e-12)
 
 
 @pytest.mark.parametrize("fmt,lam", [("f32", 5.0), ("bf16", 5.0), ("f32", 12.0)])
