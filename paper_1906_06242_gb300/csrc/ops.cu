@@ -283,77 +283,271 @@ __global__ void __launch_bounds__(kBlock) k_pair_mass(const T* pt, const T* eta,
 }
 
 // Top candidate (Section IV): the triplet of masked-in objects whose mass
-// is closest to the target, lane = event. The objects' mass terms are
-// prepared once per event (up to kCloseLocal of them; beyond that they are
-// recomputed per triplet); ties keep the first triplet in lexicographic order.
+// is closest to the target; ties keep the first triplet in lexicographic
+// order. Per-event form (one thread, the event's objects in a loop): the
+// objects' mass terms are prepared once per event (up to kCloseLocal of
+// them; beyond that they are recomputed per triplet).
 constexpr int kCloseLocal = 12;
+
+struct Closest {
+    float m;
+    int32_t a, b, c;
+};
+
+template <typename T>
+__device__ Closest closest_loop(const T* pt, const T* eta, const T* phi, const T* mass, int64_t i0, int64_t i1,
+                                const uint8_t* mask_content, float target) {
+    auto on = [&](int64_t i) { return mask_content == nullptr || mask_content[i] != 0; };
+    auto obj = [&](int64_t i) { return mass_obj(ldf(pt, i), ldf(eta, i), ldf(phi, i), ldf(mass, i)); };
+    MassObj o[kCloseLocal];
+    int32_t li[kCloseLocal];
+    int cnt = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+        if (!on(i)) continue;
+        if (cnt < kCloseLocal) {
+            o[cnt] = obj(i);
+            li[cnt] = static_cast<int32_t>(i - i0);
+        }
+        ++cnt;
+    }
+    float best_d = INFINITY;
+    Closest r{__int_as_float(0x7fc00000), -1, -1, -1};
+    if (cnt >= 3 && cnt <= kCloseLocal) {
+        for (int a = 0; a < cnt; ++a)
+            for (int b = a + 1; b < cnt; ++b)
+                for (int c = b + 1; c < cnt; ++c) {
+                    const float m = mass3obj(o[a], o[b], o[c]);
+                    const float d = fabsf(m - target);
+                    if (d < best_d) {
+                        best_d = d;
+                        r = Closest{m, li[a], li[b], li[c]};
+                    }
+                }
+    } else if (cnt > kCloseLocal) {
+        for (int64_t a = i0; a < i1; ++a) {
+            if (!on(a)) continue;
+            const MassObj oa = obj(a);
+            for (int64_t b = a + 1; b < i1; ++b) {
+                if (!on(b)) continue;
+                const MassObj ob = obj(b);
+                for (int64_t c = b + 1; c < i1; ++c) {
+                    if (!on(c)) continue;
+                    const float m = mass3obj(oa, ob, obj(c));
+                    const float d = fabsf(m - target);
+                    if (d < best_d) {
+                        best_d = d;
+                        r = Closest{m, static_cast<int32_t>(a - i0), static_cast<int32_t>(b - i0),
+                                    static_cast<int32_t>(c - i0)};
+                    }
+                }
+            }
+        }
+    }
+    return r;
+}
+
+// Warp-cooperative form. A warp takes 32 consecutive events (lane l owns
+// event l). Events with 3..kCoopMax masked-in objects are admitted in lane
+// order while the warp's objects and pairs fit its shared-memory slots; the
+// others (more objects, or past the capacity) take closest_loop. For the
+// admitted events: (A) each owner lists its masked-in objects; (B) their
+// mass terms are computed lane-parallel over the warp's objects; (C) every
+// pair term E_aE_b - p_a.p_b is computed once, lane-parallel over the warp's
+// pairs (pair (x < y) of an event in slot C(y,2) + x, colex order);
+// (D) the triplets of all admitted events are ranked lane-parallel, 32 at a
+// time (triplet (a < b < c) is rank C(c,3) + C(b,2) + a of its event), each
+// mass from three pair terms in the same order as mass3obj, with the key
+// (|m - target| bits, a << 8 | b << 4 | c) so that the minimum key is the
+// closest triplet
+// and, on ties, the first in lexicographic order; a segmented minimum over
+// the lanes holding one event's triplets goes to the owner lane. NaN
+// distances never win (their keys exceed the initial one).
+constexpr int kCoopMax = 16;      // objects per admitted event (4 bits per index in the key)
+constexpr int kCoopObj = 256;     // object slots per warp
+constexpr int kCoopPair = 1024;   // pair slots per warp
+constexpr int kCoopTri = 560;     // C(16, 3)
+constexpr int kCoopPairs16 = 120; // C(16, 2)
+
+struct CoopWarp {
+    MassObj obj[kCoopObj];
+    float pd[kCoopPair];
+    int32_t li[kCoopObj];   // local index of the object in its event
+    uint8_t ev[kCoopObj];   // owner lane of the object
+    int64_t i0[32];
+    int32_t cnt[32], obase[32], pincl[32], tincl[32];
+};
+
+inline size_t coop_smem() {
+    return static_cast<size_t>(kBlock / 32) * sizeof(CoopWarp) + kCoopTri * 2 + kCoopPairs16 * 2;
+}
+
+__device__ __forceinline__ int choose2(int k) { return k * (k - 1) / 2; }
+__device__ __forceinline__ int choose3(int k) { return k * (k - 1) * (k - 2) / 6; }
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// smallest lane l with incl[l] > q (q below incl[31])
+__device__ __forceinline__ int owner_of(const int32_t* incl, int q) {
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (incl[mid] > q) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
 
 template <typename T, typename OffT>
 __global__ void __launch_bounds__(kBlock) k_trijet_closest(const T* pt, const T* eta, const T* phi, const T* mass,
                                                            const OffT* off, int64_t n, const uint8_t* mask_rows,
                                                            const uint8_t* mask_content, float target,
                                                            float* out_mass, int32_t* out_idx3) {
-    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        if (mask_rows && !mask_rows[e]) continue;
-        const int64_t i0 = ldoff(off, e), i1 = ldoff(off, e + 1);
-        auto on = [&](int64_t i) { return mask_content == nullptr || mask_content[i] != 0; };
-        auto obj = [&](int64_t i) { return mass_obj(ldf(pt, i), ldf(eta, i), ldf(phi, i), ldf(mass, i)); };
-        MassObj o[kCloseLocal];
-        int32_t li[kCloseLocal];
+    extern __shared__ __align__(16) unsigned char smem[];
+    CoopWarp* warps = reinterpret_cast<CoopWarp*>(smem);
+    uint16_t* tri_tab = reinterpret_cast<uint16_t*>(smem + (kBlock / 32) * sizeof(CoopWarp));
+    uint16_t* pair_tab = tri_tab + kCoopTri;
+    // colex tables: rank -> (a, b, c) as a | b << 4 | c << 8, rank -> (x, y) as x | y << 4
+    for (int r = threadIdx.x; r < kCoopTri; r += blockDim.x) {
+        int c = 2;
+        while (choose3(c + 1) <= r) ++c;
+        const int rem = r - choose3(c);
+        int b = 1;
+        while (choose2(b + 1) <= rem) ++b;
+        tri_tab[r] = static_cast<uint16_t>((rem - choose2(b)) | (b << 4) | (c << 8));
+    }
+    for (int q = threadIdx.x; q < kCoopPairs16; q += blockDim.x) {
+        int y = 1;
+        while (choose2(y + 1) <= q) ++y;
+        pair_tab[q] = static_cast<uint16_t>((q - choose2(y)) | (y << 4));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    CoopWarp& W = warps[threadIdx.x >> 5];
+    auto on = [&](int64_t i) { return mask_content == nullptr || mask_content[i] != 0; };
+    const int64_t nwb = (n + 31) / 32;
+    for (int64_t wb = static_cast<int64_t>(blockIdx.x) * (kBlock / 32) + (threadIdx.x >> 5); wb < nwb;
+         wb += static_cast<int64_t>(gridDim.x) * (kBlock / 32)) {
+        const int64_t e = wb * 32 + lane;
+        const bool valid = e < n && (!mask_rows || mask_rows[e]);
+        int64_t i0 = 0, i1 = 0;
         int cnt = 0;
-        for (int64_t i = i0; i < i1; ++i) {
-            if (!on(i)) continue;
-            if (cnt < kCloseLocal) {
-                o[cnt] = obj(i);
-                li[cnt] = static_cast<int32_t>(i - i0);
-            }
-            ++cnt;
+        if (valid) {
+            i0 = ldoff(off, e);
+            i1 = ldoff(off, e + 1);
+            for (int64_t i = i0; i < i1 && cnt <= kCoopMax; ++i) cnt += on(i) ? 1 : 0;
         }
-        float best_d = INFINITY, best_m = __int_as_float(0x7fc00000);
-        int32_t ba = -1, bb = -1, bc = -1;
-        if (cnt >= 3 && cnt <= kCloseLocal) {
-            for (int a = 0; a < cnt; ++a)
-                for (int b = a + 1; b < cnt; ++b)
-                    for (int c = b + 1; c < cnt; ++c) {
-                        const float m = mass3obj(o[a], o[b], o[c]);
-                        const float d = fabsf(m - target);
-                        if (d < best_d) {
-                            best_d = d;
-                            best_m = m;
-                            ba = li[a];
-                            bb = li[b];
-                            bc = li[c];
-                        }
-                    }
-        } else if (cnt > kCloseLocal) {
-            for (int64_t a = i0; a < i1; ++a) {
-                if (!on(a)) continue;
-                const MassObj oa = obj(a);
-                for (int64_t b = a + 1; b < i1; ++b) {
-                    if (!on(b)) continue;
-                    const MassObj ob = obj(b);
-                    for (int64_t c = b + 1; c < i1; ++c) {
-                        if (!on(c)) continue;
-                        const float m = mass3obj(oa, ob, obj(c));
-                        const float d = fabsf(m - target);
-                        if (d < best_d) {
-                            best_d = d;
-                            best_m = m;
-                            ba = static_cast<int32_t>(a - i0);
-                            bb = static_cast<int32_t>(b - i0);
-                            bc = static_cast<int32_t>(c - i0);
-                        }
-                    }
+        const bool cand = valid && cnt >= 3 && cnt <= kCoopMax;
+        // admission: candidates in lane order while objects and pairs fit
+        const int oi = warp_incl_scan(cand ? cnt : 0, lane);
+        const int pi = warp_incl_scan(cand ? choose2(cnt) : 0, lane);
+        const bool admit = cand && oi <= kCoopObj && pi <= kCoopPair;
+        const int ocnt = admit ? cnt : 0;
+        const int oincl = warp_incl_scan(ocnt, lane);
+        const int pincl = warp_incl_scan(admit ? choose2(cnt) : 0, lane);
+        const int tincl = warp_incl_scan(admit ? choose3(cnt) : 0, lane);
+        const int obase = oincl - ocnt;
+        W.i0[lane] = i0;
+        W.cnt[lane] = ocnt;
+        W.obase[lane] = obase;
+        W.pincl[lane] = pincl;
+        W.tincl[lane] = tincl;
+        // (A) the admitted events' masked-in objects
+        if (admit) {
+            int k = 0;
+            for (int64_t i = i0; i < i1 && k < cnt; ++i) {
+                if (!on(i)) continue;
+                W.li[obase + k] = static_cast<int32_t>(i - i0);
+                W.ev[obase + k] = static_cast<uint8_t>(lane);
+                ++k;
+            }
+        }
+        __syncwarp();
+        const int n_obj = W.obase[31] + W.cnt[31];
+        const int n_pair = W.pincl[31];
+        const int n_tri = W.tincl[31];
+        // (B) mass terms, lane-parallel over the objects
+        for (int sidx = lane; sidx < n_obj; sidx += 32) {
+            const int64_t gi = W.i0[W.ev[sidx]] + W.li[sidx];
+            W.obj[sidx] = mass_obj(ldf(pt, gi), ldf(eta, gi), ldf(phi, gi), ldf(mass, gi));
+        }
+        __syncwarp();
+        // (C) pair terms, lane-parallel over the pairs
+        for (int q = lane; q < n_pair; q += 32) {
+            const int ow = owner_of(W.pincl, q);
+            const int local = q - (W.pincl[ow] - choose2(W.cnt[ow]));
+            const int xy = pair_tab[local];
+            const int ob = W.obase[ow];
+            W.pd[q] = pair_dot(W.obj[ob + (xy & 15)], W.obj[ob + (xy >> 4)]);
+        }
+        __syncwarp();
+        // (D) triplets, 32 at a time
+        const unsigned long long kInit = static_cast<unsigned long long>(0x7f800000u) << 32;
+        unsigned long long best = kInit;
+        const int my_texcl = tincl - (admit ? choose3(cnt) : 0);
+        for (int chunk = 0; chunk < n_tri; chunk += 32) {
+            const int t = chunk + lane;
+            int ow = 32;
+            unsigned long long key = ~0ull;
+            if (t < n_tri) {
+                ow = owner_of(W.tincl, t);
+                const int r = t - (W.tincl[ow] - choose3(W.cnt[ow]));
+                const int abc = tri_tab[r];
+                const int a = abc & 15, b = (abc >> 4) & 15, c = abc >> 8;
+                const int ob = W.obase[ow];
+                const float* pd = W.pd + (W.pincl[ow] - choose2(W.cnt[ow]));
+                const float pab = pd[choose2(b) + a], pac = pd[choose2(c) + a], pbc = pd[choose2(c) + b];
+                const float ma = W.obj[ob + a].m, mb = W.obj[ob + b].m, mc = W.obj[ob + c].m;
+                const float s3 = ma * ma + mb * mb + mc * mc;
+                const float m = sqrtf(s3 + 2.0f * (pab + pac + pbc));
+                const float d = fabsf(m - target);
+                key = (static_cast<unsigned long long>(__float_as_uint(d)) << 32) |
+                      static_cast<unsigned long long>((a << 8) | (b << 4) | c);
+            }
+            // segmented suffix minimum over lanes of the same event
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long other = __shfl_down_sync(0xffffffffu, key, o);
+                const int other_ow = __shfl_down_sync(0xffffffffu, ow, o);
+                if (lane + o < 32 && other_ow == ow && other < key) key = other;
+            }
+            // the owner takes the value of its first lane in this chunk
+            const bool mine = admit && my_texcl < chunk + 32 && tincl > chunk;
+            const int src = mine ? (my_texcl > chunk ? my_texcl - chunk : 0) : lane;
+            const unsigned long long v = __shfl_sync(0xffffffffu, key, src);
+            if (mine && v < best) best = v;
+        }
+        // outputs
+        if (valid) {
+            Closest res{__int_as_float(0x7fc00000), -1, -1, -1};
+            if (admit) {
+                if (best < kInit) {
+                    const int a = static_cast<int>((best >> 8) & 15), b = static_cast<int>((best >> 4) & 15),
+                              c = static_cast<int>(best & 15);
+                    const float* pd = W.pd + (pincl - choose2(cnt));
+                    const float pab = pd[choose2(b) + a], pac = pd[choose2(c) + a], pbc = pd[choose2(c) + b];
+                    const float ma = W.obj[obase + a].m, mb = W.obj[obase + b].m, mc = W.obj[obase + c].m;
+                    const float s3 = ma * ma + mb * mb + mc * mc;
+                    res = Closest{sqrtf(s3 + 2.0f * (pab + pac + pbc)), W.li[obase + a], W.li[obase + b],
+                                  W.li[obase + c]};
                 }
+            } else if (cnt >= 3) {
+                res = closest_loop(pt, eta, phi, mass, i0, i1, mask_content, target);
+            }
+            if (out_mass) out_mass[e] = res.m;
+            if (out_idx3) {
+                out_idx3[3 * e] = res.a;
+                out_idx3[3 * e + 1] = res.b;
+                out_idx3[3 * e + 2] = res.c;
             }
         }
-        if (out_mass) out_mass[e] = best_m;
-        if (out_idx3) {
-            out_idx3[3 * e] = ba;
-            out_idx3[3 * e + 1] = bb;
-            out_idx3[3 * e + 2] = bc;
-        }
+        __syncwarp();
     }
 }
 
@@ -1308,7 +1502,11 @@ hepacc_status hepacc_trijet_closest_mass(const void* pt, const void* eta, const 
         using O = typename decltype(ot_tag)::type;
         return with_float_type(t, [&](auto tt) -> hepacc_status {
             using T = typename decltype(tt)::type;
-            k_trijet_closest<T, O><<<flat_grid(n), kBlock, 0, s>>>(
+            const size_t smem = coop_smem();
+            int grid = 0;
+            hepacc_status st = tile_grid(k_trijet_closest<T, O>, smem, (n + 31) / 32, &grid);
+            if (st != HEPACC_OK) return st;
+            k_trijet_closest<T, O><<<grid, kBlock, smem, s>>>(
                 static_cast<const T*>(pt), static_cast<const T*>(eta), static_cast<const T*>(phi),
                 static_cast<const T*>(mass), static_cast<const O*>(offsets), n, mask_rows, mask_content, target,
                 out_mass, out_idx3);
