@@ -395,7 +395,8 @@ def main():
                      "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
                      "traffic": chain_traffic(kernel_source_sha()), "kernel": "k_chain",
                      "algorithmic_bytes_per_launch": int(alg_bytes),
-                     "avg_kernel_ms": avg_kernel_ms},
+                     "avg_kernel_ms": avg_kernel_ms,
+                     "median_kernel_ms": sorted(kern_ms)[len(kern_ms) // 2], "min_kernel_ms": min(kern_ms)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps,
