@@ -508,7 +508,7 @@ void oracle_max_pt_trijet(const void *pt, const void *eta, const void *phi, cons
         int best[3], second[3];
         double bv, sv;
         int64_t ntrip = trijet_choose(cnt, vpt, vphi, best, second, &bv, &sv);
-        if (ntrip == 0) {
+        if (ntrip == 0 || best[0] < 0) {   /* no triplet, or none with a comparable (non-NaN) value */
             if (out_mass) out_mass[ev] = NAN;
             if (out_pt) out_pt[ev] = NAN;
             if (out_idx3) out_idx3[3 * ev] = out_idx3[3 * ev + 1] = out_idx3[3 * ev + 2] = -1;
@@ -871,13 +871,17 @@ void oracle_run_chain(const oracle_batch *b, const oracle_config *c, oracle_outp
             if (njet >= 3) {
                 double bv, sv;
                 int64_t ntrip = trijet_choose(njet, jpt, jphi, tri, tri2, &bv, &sv);
-                double p3[3], e3[3], f3[3], m3[3];
-                for (int q = 0; q < 3; q++) {
-                    p3[q] = jpt[tri[q]]; e3[q] = jeta[tri[q]]; f3[q] = jphi[tri[q]]; m3[q] = jm[tri[q]];
+                /* a NaN ranking value never wins: with none comparable there
+                 * is no trijet (its variables stay NaN and are not filled) */
+                if (tri[0] >= 0) {
+                    double p3[3], e3[3], f3[3], m3[3];
+                    for (int q = 0; q < 3; q++) {
+                        p3[q] = jpt[tri[q]]; e3[q] = jeta[tri[q]]; f3[q] = jphi[tri[q]]; m3[q] = jm[tri[q]];
+                    }
+                    vars[11] = oracle_mass3(p3, e3, f3, m3);
+                    vars[12] = sqrt(bv);
+                    gap = ntrip > 1 ? (bv - sv) / bv : INFINITY;
                 }
-                vars[11] = oracle_mass3(p3, e3, f3, m3);
-                vars[12] = sqrt(bv);
-                gap = ntrip > 1 ? (bv - sv) / bv : INFINITY;
             }
             if (have_lep) {
                 vars[13] = lpt;

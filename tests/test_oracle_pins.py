@@ -631,6 +631,47 @@ def test_trijet_exact_tie_goes_to_first(orc):
     assert list(idx[0]) == [0, 1, 2] and gap[0] == 0.0
 
 
+def test_trijet_nan_phi_never_wins(orc):
+    """A NaN phi makes the ranking value of every triplet containing that
+    object NaN; such a triplet is never chosen, and with no comparable
+    triplet there is none (NaN outputs, indices -1)."""
+    nan = np.nan
+    pt = np.array([50, 40, 30, 50, 40, 30, 20, 50, 40, 30, 20], np.float32)
+    phi = np.array([0, nan, 1, 0, 1, nan, 2, nan, 1, nan, 2], np.float32)
+    z = np.zeros_like(pt)
+    mass = np.full_like(pt, 5.0)
+    off = np.array([0, 3, 7, 11], np.int64)
+    m, ptj, idx, _gap = orc.max_pt_trijet(pt, z, phi, mass, off)
+    assert np.isnan(m[0]) and np.isnan(ptj[0]) and list(idx[0]) == [-1, -1, -1]
+    assert list(idx[1]) == [0, 1, 3] and np.isfinite(m[1]) and np.isfinite(ptj[1])
+    assert np.isnan(m[2]) and np.isnan(ptj[2]) and list(idx[2]) == [-1, -1, -1]
+
+
+def test_chain_nan_phi_jet_leaves_no_trijet(orc):
+    """A selected jet with a NaN phi (it passes the Delta R cut: NaN is not
+    closer than 0.4) in an event with three selected jets: the event passes,
+    its trijet variables are NaN and its trijet histograms get nothing,
+    while the same event with a finite phi fills them."""
+    lep = {"pt": 40, "eta": 0.0, "phi": 0.0, "mass": 0.1, "charge": 1, "iso": 0.01, "tight": 1}
+    evs = []
+    for p in (np.nan, 2.5):
+        evs.append({"weight": 1.0, "mu": [lep], "el": [],
+                    "jet": [{"pt": 60, "eta": 1.5, "phi": 1.5, "mass": 5, "btag": 0.9},
+                            {"pt": 50, "eta": -1.5, "phi": float(p), "mass": 5, "btag": 0.1},
+                            {"pt": 40, "eta": 1.0, "phi": -2.0, "mass": 5, "btag": 0.1}]})
+    out = orc.run_chain(synth.hand_batch(evs), synth.CUTS, synth.HIST_SPECS, [0])
+    assert list(out["pass"][0]) == [1, 1] and list(out["njet"][0]) == [3, 3]
+    v = out["vars"][0]
+    assert np.isnan(v[11, 0]) and np.isnan(v[12, 0]) and list(out["idx"][0, 2:, 0]) == [-1, -1, -1]
+    assert np.isfinite(v[11, 1]) and np.isfinite(v[12, 1]) and list(out["idx"][0, 2:, 1]) == [0, 1, 2]
+    nb = [h[3] for h in synth.HIST_SPECS]
+    start = np.concatenate([[0], np.cumsum([b + 2 for b in nb])])
+    c = out["counts"][0]
+    assert c[start[0]:start[1]].sum() == 2                # HT: both events
+    assert c[start[11]:start[12]].sum() == 1              # trijet mass: the finite one only
+    assert c[start[12]:start[13]].sum() == 1              # trijet |sum pT|
+
+
 def test_chain_dr2_equal_to_cut_keeps_jet(orc):
     # Delta eta = 0.1f, Delta phi = 0.38729832f give Delta R^2 == 0.16f exactly in
     # IEEE binary32 (checked here with numpy's float32 arithmetic); "closer than"
