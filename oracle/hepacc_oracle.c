@@ -401,7 +401,7 @@ static p4_t p4_add(p4_t a, p4_t b)
 static double p4_mass(p4_t v)
 {
     double m2 = v.e * v.e - (v.px * v.px + v.py * v.py + v.pz * v.pz);
-    return sqrt(m2 > 0.0 ? m2 : 0.0);
+    return sqrt(m2 < 0.0 ? 0.0 : m2);   /* rounding below 0 clamps; NaN stays NaN */
 }
 
 double oracle_mass2(double pt1, double eta1, double phi1, double m1,

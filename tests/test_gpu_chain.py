@@ -78,6 +78,33 @@ def test_chain_many_jets_and_leptons(H, orc):
     check(H, orc, batch, [0, 4, -4])
 
 
+def test_chain_nan_phi_jets(H, orc):
+    """Jets with a NaN phi are selected (NaN is not closer than the Delta R
+    cut) and make the ranking value of every triplet that contains them NaN;
+    a NaN value never wins, so events whose triplets are all NaN-ranked have
+    no trijet on either side (per event and in the histograms)."""
+    batch = synth.generate(20_011, 7)
+    phi = batch.cols["jet_phi"].copy()
+    phi[np.random.default_rng(8).random(len(phi)) < 0.2] = np.nan
+    cols = dict(batch.cols)
+    cols["jet_phi"] = phi
+    nb = synth.EventBatch(n_events=batch.n_events, jet_offsets=batch.jet_offsets, mu_offsets=batch.mu_offsets,
+                          el_offsets=batch.el_offsets, cols=cols, weight=batch.weight, seed=batch.seed)
+    check(H, orc, nb, [0, 3])
+    o = orc.run_chain(nb, synth.CUTS, synth.HIST_SPECS, [0, 3])
+    assert ((o["pass"] == 1) & (o["njet"] >= 3) & (o["idx"][:, 2] < 0)).sum() > 0   # the case occurs
+    # the per-operation kernel on the same jets
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    om, _opt, oidx, _gap = orc.max_pt_trijet(cols["jet_pt"], cols["jet_eta"], phi, cols["jet_mass"], batch.jet_offsets)
+    gm, _gpt, gidx = H.hepacc_max_pt_trijet(d(cols["jet_pt"]), d(cols["jet_eta"]), d(phi), d(cols["jet_mass"]),
+                                            d(batch.jet_offsets))
+    torch.cuda.synchronize()
+    gidx = gidx.cpu().numpy()
+    np.testing.assert_array_equal(gidx[:, 0] < 0, oidx[:, 0] < 0)
+    assert (np.isnan(gm.cpu().numpy()) == np.isnan(om)).all()
+    assert H.device_error() == 0
+
+
 def test_chain_histograms_without_per_event_outputs(H, orc):
     # the launch the benchmark times (no per-event outputs) against the oracle
     batch = synth.generate(200_003, 7)

@@ -631,6 +631,14 @@ def test_trijet_exact_tie_goes_to_first(orc):
     assert list(idx[0]) == [0, 1, 2] and gap[0] == 0.0
 
 
+def test_mass_of_nan_coordinates_is_nan(orc):
+    """Invariant masses propagate a NaN coordinate (the clamp at zero is for
+    rounding below zero only)."""
+    assert math.isnan(orc.mass2(50.0, 0.0, float("nan"), 5.0, 40.0, 1.0, 1.0, 5.0))
+    assert math.isnan(orc.mass2(50.0, float("nan"), 0.0, 5.0, 40.0, 1.0, 1.0, 5.0))
+    assert orc.mass2(50.0, 0.3, 0.2, 0.0, 50.0, 0.3, 0.2, 0.0) == 0.0   # collinear massless pair
+
+
 def test_trijet_nan_phi_never_wins(orc):
     """A NaN phi makes the ranking value of every triplet containing that
     object NaN; such a triplet is never chosen, and with no comparable
