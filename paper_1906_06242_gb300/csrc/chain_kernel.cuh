@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
                 p_ls = pair_dot(ol, os);
                 var[7] = sqrtf(ol.m * ol.m + os.m * os.m + 2.0f * p_ls);
             }
-            if (njet >= 3) {
+            if (njet >= 3 && ta >= 0) {
                 // the triplet's four-momenta; jets shared with the leading pair reuse its terms
                 auto obj = [&](int idx, int w) {
                     if (idx == lead) return ol;
@@ -927,10 +927,13 @@ __global__ void __launch_bounds__(FORM == F_SAMPLES ? kMaxThreadsBatched : kMaxT
             if (mine) {
                 int ta = -1, tb = -1, tc = -1;
                 if (nsel >= 3 && nsel <= kScratch) {
-                    const int16_t* li = reinterpret_cast<const int16_t*>(r);
-                    ta = li[key >> 8];
-                    tb = li[(key >> 4) & 15];
-                    tc = li[key & 15];
+                    // key 0xfff: every triplet's value was NaN (a NaN phi), no triplet
+                    if (key != 0xfff) {
+                        const int16_t* li = reinterpret_cast<const int16_t*>(r);
+                        ta = li[key >> 8];
+                        tb = li[(key >> 4) & 15];
+                        tc = li[key & 15];
+                    }
                 } else if (nsel > kScratch) {
                     if (staged)
                         slow_triplet(sc, ev, s, best, ta, tb, tc);
