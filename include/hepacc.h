@@ -213,10 +213,11 @@ hepacc_status hepacc_fill_histogram(const void *data, hepacc_dtype data_type, co
  * (nbins[2]+2) + b_2) ...; counts, sumw and sumw2 have prod_d (nbins[d]+2)
  * <= 2^24 entries (sumw, sumw2 may be NULL), and counts[c] += 1,
  * sumw[c] += w, sumw2[c] += w*w with the accuracy of the one-dimensional
- * fill (exact per block up to about 250 cells with sumw2, 760 without). Elements with
- * mask[j] unset or a NaN on any axis are not filled. data, data_types, edges
- * and nbins are HOST arrays of ndim entries (data[d] and edges[d] are device
- * pointers), read before the call returns. 1 <= nbins[d] <= 65536. */
+ * fill (exact per block up to about 250 cells with sumw2, 760 without).
+ * Elements with mask[j] unset or a NaN on any axis are not filled. data,
+ * data_types, edges and nbins are HOST arrays of ndim entries (data[d] and
+ * edges[d] are device pointers), read before the call returns.
+ * 1 <= nbins[d] <= 65536. */
 #define HEPACC_MAX_HIST_DIMS 4
 hepacc_status hepacc_fill_histogram_nd(int32_t ndim, const void *const *data, const hepacc_dtype *data_types,
                                        const float *const *edges, const int32_t *nbins, const float *weights,
