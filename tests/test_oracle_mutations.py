@@ -40,6 +40,7 @@ MUTATIONS = [
     ("lookup centre is the lower edge", "float cb = (edges[b - 1] + edges[b]) * 0.5f;", "float cb = edges[b - 1];"),
     ("nd stride drops the flow bins", "cell = cell * (nbins[d] + 2) + b;", "cell = cell * (nbins[d] + 1) + b;"),
     ("nd NaN goes to underflow", "skip = 1;\n                break;", "b = 0;"),
+    ("nd cell order reversed", "for (int d = 0; d < ndim; d++) {", "for (int d = ndim - 1; d >= 0; d--) {"),
 ]
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
