@@ -41,6 +41,7 @@ MUTATIONS = [
     ("nd stride drops the flow bins", "cell = cell * (nbins[d] + 2) + b;", "cell = cell * (nbins[d] + 1) + b;"),
     ("nd NaN goes to underflow", "skip = 1;\n                break;", "b = 0;"),
     ("nd cell order reversed", "for (int d = 0; d < ndim; d++) {", "for (int d = ndim - 1; d >= 0; d--) {"),
+    ("mass clamp maps NaN to 0", "return sqrt(m2 < 0.0 ? 0.0 : m2);", "return sqrt(m2 > 0.0 ? m2 : 0.0);"),
 ]
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
