@@ -315,6 +315,10 @@ typedef struct {
     /* Mean jets, muons and electrons per event, used only to size the
      * shared-memory staging of each collection; 0 selects 6, 1 and 1. */
     float jets_per_event, muons_per_event, electrons_per_event;
+    /* Content lengths of the jet, muon and electron columns (elements, >= 0).
+     * The debug checks (HEPACC_DEBUG, HEPACC_PLAN_VALIDATE) reject a batch
+     * whose offsets[n_events] exceeds them before anything reads a column. */
+    int64_t jet_len, mu_len, el_len;
 } hepacc_event_batch;
 
 /* Cuts, jet-pt scale variations and the 20 histograms. HOST memory: the call
@@ -368,8 +372,11 @@ typedef struct {
  * One kernel launch; each input column is read once.
  * Debug checks: with the environment variable HEPACC_DEBUG set (and not 0)
  * the three offsets arrays are first checked on the device (offsets[0] >= 0,
- * non-decreasing; the call waits for the check); a failure returns
- * HEPACC_ERR_DEVICE_CHECK before the chain is launched. */
+ * non-decreasing, offsets[n_events] <= the collection's content length; the
+ * call waits for the check); a failure returns HEPACC_ERR_DEVICE_CHECK
+ * before the chain is launched.
+ * Shared memory: the call uses up to the device's per-block opt-in limit
+ * (one resident block per SM). */
 hepacc_status hepacc_run_chain(const hepacc_event_batch *batch, const hepacc_chain_config *config,
                                const hepacc_chain_outputs *out, hepacc_stream stream);
 
@@ -394,9 +401,10 @@ typedef struct hepacc_plan hepacc_plan;
 /* Builds a plan that runs the chain of hepacc_run_chain over samples[0..n)
  * with one configuration, up to sixteen samples per persistent launch. With
  * global histograms the samples' tiles form one range that the blocks share
- * (no block waits at a sample boundary); with shared-memory histograms
- * every block walks through the samples in turn and adds its histograms to
- * a sample's outputs when done with it. Sample i adds to outputs[i]
+ * (no block waits at a sample boundary; the kernel of hepacc_run_chain,
+ * with a choice of stage counts); with shared-memory histograms every block
+ * walks through the samples in turn and adds its histograms to a sample's
+ * outputs when done with it. Sample i adds to outputs[i]
  * (counts, sumw, sumw2 as in
  * hepacc_run_chain; per-event arrays must be NULL). All samples use I64
  * offsets and the same kin_type and btag_type (F32 with F32, F16 with F16
@@ -409,7 +417,7 @@ typedef struct hepacc_plan hepacc_plan;
  * here must be valid), the fastest kept, and the outputs cleared to zero
  * afterwards, on `stream`, which the call synchronises. config is HOST
  * memory and copied; the sample and output structs are copied; the device
- * buffers they point to must stay valid for the plan's life. With
+ * buffers they point to must stay valid while runs use them. With
  * HEPACC_PLAN_VALIDATE (or HEPACC_DEBUG set, as for hepacc_run_chain) every
  * sample's offsets are checked first; a failure returns
  * HEPACC_ERR_DEVICE_CHECK and nothing runs. *plan is NULL on error. */
@@ -417,12 +425,23 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config *config, int32_t n_sa
                                  const hepacc_event_batch *samples, const hepacc_chain_outputs *outputs,
                                  int32_t flags, hepacc_stream stream, hepacc_plan **plan);
 
-/* Runs the plan once on `stream` (outputs accumulate). Not thread-safe on
- * one plan; two runs of one plan on different streams race on its outputs. */
-hepacc_status hepacc_plan_run(hepacc_plan *plan, hepacc_stream stream);
+/* Runs the plan once on `stream` (outputs accumulate). With samples and
+ * outputs NULL it runs the samples and outputs the plan was created with.
+ * Otherwise it runs the same chain, configuration and (with
+ * HEPACC_PLAN_GRAPH) captured graph over another batch of n_samples
+ * samples and their outputs (Section II: the cache is processed in
+ * batches): n_samples must equal the plan's, the column types must match;
+ * event counts may differ (the graph's kernel nodes are given the new
+ * samples' descriptors before the replay). The structs are read before the
+ * call returns; the device buffers must stay valid until the run is done.
+ * Not thread-safe on one plan; two runs of one plan on different streams
+ * race on their outputs if they share them. */
+hepacc_status hepacc_plan_run(hepacc_plan *plan, int32_t n_samples, const hepacc_event_batch *samples,
+                              const hepacc_chain_outputs *outputs, hepacc_stream stream);
 
-/* Writes a one-line JSON description of the chosen configuration into
- * buf[0..len) (NUL-terminated, truncated to fit). */
+/* Writes a one-line JSON description of the chosen configuration and of
+ * every candidate the autotuner timed into buf[0..len) (NUL-terminated,
+ * truncated to fit). */
 hepacc_status hepacc_plan_describe(const hepacc_plan *plan, char *buf, int32_t len);
 
 /* Frees the plan (NULL is allowed); outputs and inputs are not touched. */

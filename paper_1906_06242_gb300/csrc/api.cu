@@ -7,11 +7,23 @@
 
 namespace hepacc {
 
-unsigned int tu_error_ops(bool clear);
-unsigned int tu_error_chain(bool clear);
-
 namespace {
 thread_local std::string t_last_error;
+
+struct ErrorWords {
+    std::mutex mu;
+    std::vector<ErrorWordReader> readers;
+};
+ErrorWords& error_words() {
+    static ErrorWords w;
+    return w;
+}
+}  // namespace
+
+void register_error_word(ErrorWordReader reader) {
+    ErrorWords& w = error_words();
+    std::lock_guard<std::mutex> g(w.mu);
+    w.readers.push_back(reader);
 }
 
 hepacc_status fail(hepacc_status s, const char* fmt, ...) {
@@ -83,7 +95,13 @@ hepacc_status hepacc_device_error(uint32_t* flags) {
     if (!flags) return fail(HEPACC_ERR_INVALID_ARG, "flags is NULL");
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    *flags = tu_error_ops(true) | tu_error_chain(true);
+    unsigned int v = 0;
+    {
+        ErrorWords& w = error_words();
+        std::lock_guard<std::mutex> g(w.mu);
+        for (ErrorWordReader r : w.readers) v |= r(true);
+    }
+    *flags = v;
     return HEPACC_OK;
 }
 

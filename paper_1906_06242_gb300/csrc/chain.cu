@@ -1,21 +1,16 @@
 // Host side of the fused chain: validates calls, prepares the kernel
 // parameters (cuts, scales, histogram edges), chooses the shared-memory
-// layout and the histogram placement and launches the kernel for the column
-// types; batched plans (many samples per launch, autotuned, replayed as a
-// CUDA graph).
+// layout and launches the compacting kernel (fused_kernel.cuh) for the column
+// types; batched plans (many samples per launch, autotuned over block
+// layouts and histogram placements, replayed as a CUDA graph, reusable over
+// new batches of the same shape).
 #include <cmath>
 #include <new>
 #include <vector>
 
-#include "chain_kernel.cuh"
+#include "fused_kernel.cuh"
 
 namespace hepacc {
-
-unsigned int tu_error_chain(bool clear) {
-    return chain::tu_error_f32(clear) | chain::tu_error_bf16(clear) | chain::tu_error_f16(clear) |
-           chain::tu_error_batched_f32(clear) | chain::tu_error_batched_bf16(clear) |
-           chain::tu_error_batched_f16(clear);
-}
 
 namespace chain {
 namespace {
@@ -70,6 +65,7 @@ hepacc_status check_batch(const hepacc_event_batch* b) {
     if (!is_offsets_type(b->offsets_type)) return fail(HEPACC_ERR_DTYPE, "offsets must be I32 or I64");
     if (!is_float_type(b->kin_type)) return fail(HEPACC_ERR_DTYPE, "kin_type must be F32, F16 or BF16");
     if (b->btag_type != HEPACC_F32 && b->btag_type != HEPACC_F16) return fail(HEPACC_ERR_DTYPE, "btag_type must be F32 or F16");
+    if (b->jet_len < 0 || b->mu_len < 0 || b->el_len < 0) return fail(HEPACC_ERR_INVALID_ARG, "negative content length");
     if (b->n_events > 0 &&
         (!b->jet_offsets || !b->mu_offsets || !b->el_offsets || !b->weight || !b->jet_pt || !b->jet_eta ||
          !b->jet_phi || !b->jet_mass || !b->jet_btag || !b->mu_pt || !b->mu_eta || !b->mu_phi || !b->mu_iso ||
@@ -78,11 +74,13 @@ hepacc_status check_batch(const hepacc_event_batch* b) {
     return HEPACC_OK;
 }
 
-// The three offsets arrays of a batch checked on the device (debug checks).
+// The three offsets arrays of a batch checked on the device against their
+// content lengths (debug checks).
 hepacc_status check_batch_offsets(const hepacc_event_batch* b, cudaStream_t s) {
     const void* offs[3] = {b->jet_offsets, b->mu_offsets, b->el_offsets};
-    for (const void* o : offs) {
-        const hepacc_status st = check_offsets_nondecreasing(o, b->offsets_type, b->n_events, s);
+    const int64_t lens[3] = {b->jet_len, b->mu_len, b->el_len};
+    for (int c = 0; c < 3; ++c) {
+        const hepacc_status st = check_offsets(offs[c], b->offsets_type, b->n_events, lens[c], s);
         if (st != HEPACC_OK) return st;
     }
     return HEPACC_OK;
@@ -198,18 +196,127 @@ bool layout_for(int E, int hmode, int cluster, double lam_j, double lam_m, doubl
     return L.total <= std::min(per_block, static_cast<size_t>(di.smem_optin));
 }
 
-hepacc_status dispatch(hepacc_dtype kin, bool batched, const LaunchArgs& a) {
-    if (batched) {
-        switch (kin) {
-            case HEPACC_F32: return run_batched_f32(a);
-            case HEPACC_F16: return run_batched_f16(a);
-            default: return run_batched_bf16(a);
-        }
-    }
+// Shared-memory layout of the compacting kernel for blocks (and tiles) of NT
+// threads with S stages: stage capacities from the mean objects per event
+// (a tile that does not fit is read from global memory), the edges, scales
+// and (flat launches) sample descriptors, then the buffer of passing events
+// and their jets in what is left of the block's shared memory (at most
+// 2 NT events). Returns whether it fits with room for at least 4 x 32 jets.
+bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_t kes, size_t bes, const ChainParams& P,
+                  int flat_samples, int blocks_per_sm, fused::FLayout& L) {
+    std::memset(&L, 0, sizeof L);
+    if (S < 2 || S > fused::kMaxStages) return false;
+    auto cap_of = [&](double lam) {
+        const double m = NT * lam;
+        return static_cast<uint32_t>(((static_cast<size_t>(m + 4.0 * std::sqrt(m) + 64.0)) + 31) & ~size_t(31));
+    };
+    const uint32_t cj = cap_of(lam_j), cm = cap_of(lam_m), ce = cap_of(lam_e);
+    uint32_t off = 0;
+    auto add = [&](int c, size_t es, int coll, uint32_t cap) {
+        ColSpec& cs = L.col[c];
+        cs.base = nullptr;
+        cs.es = static_cast<uint32_t>(es);
+        cs.coll = static_cast<uint32_t>(coll);
+        cs.cap = static_cast<uint32_t>((cap * es + 32 + 15) & ~size_t(15));
+        cs.soff = off;
+        off += cs.cap;
+    };
+    add(J_PT, kes, 0, cj);
+    add(J_ETA, kes, 0, cj);
+    add(J_PHI, kes, 0, cj);
+    add(J_MASS, kes, 0, cj);
+    add(J_BTAG, bes, 0, cj);
+    add(M_PT, kes, 1, cm);
+    add(M_ETA, kes, 1, cm);
+    add(M_PHI, kes, 1, cm);
+    add(M_ISO, 4, 1, cm);
+    add(M_TIGHT, 1, 1, cm);
+    add(E_PT, kes, 2, ce);
+    add(E_ETA, kes, 2, ce);
+    add(E_PHI, kes, 2, ce);
+    add(E_ISO, 4, 2, ce);
+    add(E_TIGHT, 1, 2, ce);
+    auto region = [](size_t& at, size_t bytes) {
+        at = (at + 15) & ~size_t(15);
+        const uint32_t start = static_cast<uint32_t>(at);
+        at += bytes;
+        return start;
+    };
+    L.stages = S;
+    L.stage_bytes = static_cast<uint32_t>((fused::kHdrBytes + off + 127) & ~size_t(127));
+    size_t at = 0;
+    region(at, static_cast<size_t>(S) * L.stage_bytes);
+    L.bars = region(at, 8 * fused::kMaxStages + 6 * 8);
+    L.edges = region(at, static_cast<size_t>(P.n_edges) * 4);
+    L.scales = region(at, static_cast<size_t>(P.n_var) * 4);
+    L.samples = region(at, static_cast<size_t>(flat_samples) * sizeof(SampleDesc));
+    L.misc = region(at, (4 + 32) * 4);
+    const DeviceInfo di = device_info();
+    const size_t limit =
+        std::min(static_cast<size_t>(di.smem_per_sm / blocks_per_sm - di.smem_reserved), static_cast<size_t>(di.smem_optin));
+    const size_t slack = 16 * 24;   // alignment of the buffer's regions
+    if (at + slack >= limit) return false;
+    const size_t avail = limit - at - slack;
+    const size_t per_ev = 11 * 4 + 2 * 8, per_j = 7 * 4 + 1;
+    int cap_ev = std::min(2 * NT, 65535);
+    if (static_cast<size_t>(cap_ev) * per_ev + 4 * 32 * per_j > avail) cap_ev = NT;
+    if (static_cast<size_t>(cap_ev) * per_ev + 4 * 32 * per_j > avail) return false;
+    const int cap_j = static_cast<int>(std::min<size_t>((avail - cap_ev * per_ev) / per_j, 65535));
+    L.cap_ev = cap_ev;
+    L.cap_j = cap_j;
+    const size_t ne = static_cast<size_t>(cap_ev), nj = static_cast<size_t>(cap_j);
+    L.b_q = region(at, ne * 8);
+    L.b_p = region(at, ne * 8);
+    L.b_e = region(at, ne * 4);
+    L.b_s = region(at, ne * 4);
+    L.b_w = region(at, ne * 4);
+    L.b_lpt = region(at, ne * 4);
+    L.b_leta = region(at, ne * 4);
+    L.b_lphi = region(at, ne * 4);
+    L.b_liso = region(at, ne * 4);
+    L.b_nlep = region(at, ne * 4);
+    L.b_j0 = region(at, ne * 4);
+    L.b_nj = region(at, ne * 4);
+    L.b_ps = region(at, ne * 4);
+    L.j_pt = region(at, nj * 4);
+    L.j_eta = region(at, nj * 4);
+    L.j_phi = region(at, nj * 4);
+    L.j_m = region(at, nj * 4);
+    L.j_bt = region(at, nj * 4);
+    L.j_c = region(at, nj * 4);
+    L.j_s = region(at, nj * 4);
+    L.j_acc = region(at, nj);
+    L.total = static_cast<uint32_t>((at + 15) & ~size_t(15));
+    return L.total <= limit;
+}
+
+// The configuration of single-sample launches (hepacc_run_chain): blocks of
+// kDebugBlock threads laid out for two blocks per SM with two stages (the
+// rest of the shared memory goes to the pair buffer; measured fastest on
+// GB300 for the 10M-event FP32 set: 2.56 ms against 3.16 ms with three
+// stages and 3.30 ms for one block of 256 per SM); one block per SM if that
+// does not fit.
+bool single_config(double lam_j, double lam_m, double lam_e, size_t kes, size_t bes, const ChainParams& P,
+                   fused::FLayout& L, int& NT) {
+    NT = fused::kDebugBlock;
+    const int bps = 2;
+    if (fused_layout(NT, 2, lam_j, lam_m, lam_e, kes, bes, P, 0, bps, L)) return true;
+    return fused_layout(NT, 2, lam_j, lam_m, lam_e, kes, bes, P, 0, 1, L);
+}
+
+hepacc_status dispatch_fused(hepacc_dtype kin, const fused::FusedArgs& a) {
     switch (kin) {
-        case HEPACC_F32: return run_f32(a);
-        case HEPACC_F16: return run_f16(a);
-        default: return run_bf16(a);
+        case HEPACC_F32: return fused::run_fused_f32(a);
+        case HEPACC_F16: return fused::run_fused_f16(a);
+        default: return fused::run_fused_bf16(a);
+    }
+}
+
+hepacc_status dispatch_walking(hepacc_dtype kin, const LaunchArgs& a) {
+    switch (kin) {
+        case HEPACC_F32: return run_batched_f32(a);
+        case HEPACC_F16: return run_batched_f16(a);
+        default: return run_batched_bf16(a);
     }
 }
 
@@ -243,74 +350,120 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     const double lam_m = b->muons_per_event > 0 ? b->muons_per_event : 1.0;
     const double lam_e = b->electrons_per_event > 0 ? b->electrons_per_event : 1.0;
     const size_t kes = dtype_size(b->kin_type), bes = dtype_size(b->btag_type);
-    Layout L;
-    int E = 0, hmode = H_GLOBAL;
-    // blocks per SM as built for, else one; the largest block that fits.
-    // Histograms in global memory: measured faster here than block-private
-    // shared-memory copies, whose fill serialises each histogram on one lane
-    for (int bps = kMinBlocks; bps >= 1 && E == 0; bps = bps > 1 ? 1 : 0)
-        for (int e = kMaxThreads; e >= 64 && E == 0; e -= 32)
-            if (layout_for(e, H_GLOBAL, 1, lam_j, lam_m, lam_e, kes, bes, bps, P, L)) E = e;
-    if (E == 0) return fail(HEPACC_ERR_INVALID_ARG, "chain stage buffers do not fit in shared memory");
+    fused::FLayout L;
+    int NT = 0;
+    if (!single_config(lam_j, lam_m, lam_e, kes, bes, P, L, NT))
+        return fail(HEPACC_ERR_INVALID_ARG, "chain stage buffers do not fit in shared memory");
 
-    LaunchArgs a;
+    fused::FusedArgs a;
     a.layout = L;
     a.P = &P;
     a.B = &B;
     a.offsets_type = b->offsets_type;
     a.btag_type = b->btag_type;
     a.debug = has_per_event(out);
-    a.hmode = hmode;
-    a.block = E;
-    a.cluster = 1;
+    a.flat = false;
+    a.block = NT;
     a.grid = 0;
-    a.max_tiles = (b->n_events + E - 1) / E;
+    a.cap_grid = true;
+    a.ntiles = (b->n_events + NT - 1) / NT;
     a.stream = reinterpret_cast<cudaStream_t>(stream);
-    return dispatch(b->kin_type, false, a);
+    return dispatch_fused(b->kin_type, a);
 }
 
 // ---------------------------------------------------------------------------
 // Batched plans
 // ---------------------------------------------------------------------------
 
+namespace {
+
+// A kernel configuration of a plan: the compacting kernel over the samples'
+// tiles as one flat range (global histograms; block layout with S stages),
+// or the walking kernel with shared-memory histograms in one block or spread
+// over a cluster.
+struct Candidate {
+    bool compacting;
+    int hmode, cluster, block, blocks_per_sm, stages;
+    Layout L;            // walking kernel
+    fused::FLayout FL;   // compacting kernel
+};
+
+}  // namespace
+
 struct hepacc_plan {
     ChainParams P;
-    std::vector<BatchDesc> launches;   // up to kMaxSamples samples each
+    int n_samples;
     std::vector<hepacc_chain_outputs> outs;
+    std::vector<hepacc_event_batch> samples;
     hepacc_dtype kin, btag;
-    int64_t max_events;
-    int hmode, block, cluster;         // the chosen configuration
-    Layout L;
+    Candidate c;         // the chosen configuration
     float tuned_ms;
     int n_candidates;
+    std::vector<std::string> tried;   // candidate descriptions and times (JSON fragments)
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    std::vector<cudaGraphNode_t> nodes;   // the graph's kernel nodes, one per launch, in launch order
 };
 
 namespace {
 
-hepacc_status plan_launch(const hepacc_plan* p, cudaStream_t s) {
-    for (const BatchDesc& B0 : p->launches) {
+// The launches of a set of samples: up to kMaxSamples per launch.
+std::vector<BatchDesc> make_launches(int n, const hepacc_event_batch* samples, const hepacc_chain_outputs* outs,
+                                     int block) {
+    std::vector<BatchDesc> v;
+    for (int i0 = 0; i0 < n; i0 += kMaxSamples) {
+        BatchDesc B;
+        std::memset(&B, 0, sizeof B);
+        B.n_samples = std::min(kMaxSamples, n - i0);
+        for (int j = 0; j < B.n_samples; ++j) make_sample(&samples[i0 + j], &outs[i0 + j], B.s[j]);
         // flat launches: the first tile of every sample for this block size
-        BatchDesc B = B0;
         B.tile_start[0] = 0;
-        for (int i = 0; i < B.n_samples; ++i)
-            B.tile_start[i + 1] = B.tile_start[i] + (B.s[i].n + p->block - 1) / p->block;
-        LaunchArgs a;
-        a.layout = p->L;
+        for (int i = 0; i < B.n_samples; ++i) B.tile_start[i + 1] = B.tile_start[i] + (B.s[i].n + block - 1) / block;
+        v.push_back(B);
+    }
+    return v;
+}
+
+// Launches one BatchDesc with the plan's configuration. The grid is the
+// full persistent grid whatever the sizes, so that a captured launch can be
+// pointed at other samples.
+hepacc_status launch_one(const hepacc_plan* p, const Candidate& c, const BatchDesc& B, cudaStream_t s) {
+    if (c.compacting) {
+        fused::FusedArgs a;
+        a.layout = c.FL;
         a.P = &p->P;
         a.B = &B;
         a.offsets_type = HEPACC_I64;
         a.btag_type = p->btag;
         a.debug = false;
-        a.hmode = p->hmode;
-        a.block = p->block;
-        a.cluster = p->cluster;
+        a.flat = true;
+        a.block = c.block;
         a.grid = 0;
-        a.max_tiles = std::max<int64_t>(1, p->hmode == H_GLOBAL ? B.tile_start[B.n_samples]
-                                                               : (p->max_events + p->block - 1) / p->block);
+        a.cap_grid = false;
+        a.ntiles = B.tile_start[B.n_samples];
         a.stream = s;
-        const hepacc_status st = dispatch(p->kin, true, a);
+        return dispatch_fused(p->kin, a);
+    }
+    LaunchArgs a;
+    a.layout = c.L;
+    a.P = &p->P;
+    a.B = &B;
+    a.offsets_type = HEPACC_I64;
+    a.btag_type = p->btag;
+    a.debug = false;
+    a.hmode = c.hmode;
+    a.block = c.block;
+    a.cluster = c.cluster;
+    a.grid = 0;
+    a.max_tiles = int64_t(1) << 40;
+    a.stream = s;
+    return dispatch_walking(p->kin, a);
+}
+
+hepacc_status plan_launch(const hepacc_plan* p, const Candidate& c, const std::vector<BatchDesc>& launches,
+                          cudaStream_t s) {
+    for (const BatchDesc& B : launches) {
+        const hepacc_status st = launch_one(p, c, B, s);
         if (st != HEPACC_OK) return st;
     }
     return HEPACC_OK;
@@ -327,10 +480,17 @@ hepacc_status zero_outputs(const hepacc_plan* p, cudaStream_t s) {
     return HEPACC_OK;
 }
 
-struct Candidate {
-    int hmode, cluster, block;
-    Layout L;
-};
+std::string describe(const Candidate& c) {
+    char buf[160];
+    if (c.compacting)
+        snprintf(buf, sizeof buf, "{\"kernel\": \"compacting\", \"histograms\": \"global\", \"block\": %d, "
+                 "\"blocks_per_sm\": %d, \"stages\": %d, \"buffer_events\": %d, \"buffer_jets\": %d", c.block,
+                 c.blocks_per_sm, c.stages, c.FL.cap_ev, c.FL.cap_j);
+    else
+        snprintf(buf, sizeof buf, "{\"kernel\": \"walking\", \"histograms\": \"%s\", \"cluster\": %d, \"block\": %d",
+                 c.hmode == H_SMEM ? "block" : "cluster", c.cluster, c.block);
+    return buf;
+}
 
 // Times every candidate (one warm-up run, two timed) on the plan's samples
 // and returns the index of the fastest, -1 if none ran.
@@ -343,46 +503,98 @@ int autotune(hepacc_plan* p, const std::vector<Candidate>& cands, cudaStream_t s
     int pick = -1;
     best_ms = -1.0f;
     for (size_t i = 0; i < cands.size(); ++i) {
-        p->hmode = cands[i].hmode;
-        p->cluster = cands[i].cluster;
-        p->block = cands[i].block;
-        p->L = cands[i].L;
-        if (plan_launch(p, s) != HEPACC_OK) continue;
+        const auto launches = make_launches(p->n_samples, p->samples.data(), p->outs.data(), cands[i].block);
+        std::string d = describe(cands[i]);
+        if (plan_launch(p, cands[i], launches, s) != HEPACC_OK) {
+            cudaGetLastError();
+            p->tried.push_back(d + ", \"ms\": null}");
+            continue;
+        }
         cudaEventRecord(e0, s);
-        const bool ok = plan_launch(p, s) == HEPACC_OK && plan_launch(p, s) == HEPACC_OK;
+        const bool ok = plan_launch(p, cands[i], launches, s) == HEPACC_OK && plan_launch(p, cands[i], launches, s) == HEPACC_OK;
         cudaEventRecord(e1, s);
         float ms = 0.0f;
-        if (cudaEventSynchronize(e1) == cudaSuccess && ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-            (best_ms < 0.0f || ms < best_ms)) {
-            best_ms = ms;
-            pick = static_cast<int>(i);
+        if (cudaEventSynchronize(e1) == cudaSuccess && ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            ms *= 0.5f;
+            char t[48];
+            snprintf(t, sizeof t, ", \"ms\": %.4f}", static_cast<double>(ms));
+            p->tried.push_back(d + t);
+            if (best_ms < 0.0f || ms < best_ms) {
+                best_ms = ms;
+                pick = static_cast<int>(i);
+            }
+        } else {
+            cudaGetLastError();
+            p->tried.push_back(d + ", \"ms\": null}");
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (pick >= 0) best_ms *= 0.5f;
     return pick;
 }
 
+// Captures the plan's launches into a graph and records its kernel nodes in
+// launch order (the capture of one stream is a chain).
 hepacc_status capture(hepacc_plan* p) {
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "capture stream");
     hepacc_status st = HEPACC_OK;
+    const auto launches = make_launches(p->n_samples, p->samples.data(), p->outs.data(), p->c.block);
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        st = plan_launch(p, cs);
+        st = plan_launch(p, p->c, launches, cs);
         const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
         if (st == HEPACC_OK && e2 != cudaSuccess) st = cuda_fail(e2, "graph capture");
     } else {
         st = cuda_fail(e, "begin capture");
     }
-    if (st == HEPACC_OK) {
-        e = cudaGraphInstantiate(&p->exec, p->graph, 0);
-        if (e != cudaSuccess) st = cuda_fail(e, "graph instantiate");
-    }
     cudaStreamDestroy(cs);
-    return st;
+    if (st != HEPACC_OK) return st;
+    size_t nroots = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphGetRootNodes(p->graph, &node, &nroots);
+    if (e != cudaSuccess) return cuda_fail(e, "graph roots");
+    while (node) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(node, &t);
+        if (e != cudaSuccess) return cuda_fail(e, "graph node type");
+        if (t == cudaGraphNodeTypeKernel) p->nodes.push_back(node);
+        size_t nd = 0;
+        e = cudaGraphNodeGetDependentNodes(node, nullptr, nullptr, &nd);
+        if (e != cudaSuccess) return cuda_fail(e, "graph node dependents");
+        if (nd > 1) return fail(HEPACC_ERR_CUDA, "plan graph is not a chain");
+        cudaGraphNode_t nx = nullptr;
+        if (nd == 1) {
+            e = cudaGraphNodeGetDependentNodes(node, &nx, nullptr, &nd);
+            if (e != cudaSuccess) return cuda_fail(e, "graph node dependents");
+        }
+        node = nx;
+    }
+    if (p->nodes.size() != launches.size()) return fail(HEPACC_ERR_CUDA, "plan graph has %zu kernel nodes for %zu launches",
+                                                        p->nodes.size(), launches.size());
+    e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    return HEPACC_OK;
+}
+
+// Checks a set of samples against a plan's: count, types; outputs given.
+hepacc_status check_plan_samples(int n_samples, const hepacc_event_batch* samples, const hepacc_chain_outputs* outputs,
+                                 hepacc_dtype kin, hepacc_dtype btag) {
+    for (int i = 0; i < n_samples; ++i) {
+        const hepacc_event_batch& b = samples[i];
+        const hepacc_chain_outputs& o = outputs[i];
+        hepacc_status st = check_batch(&b);
+        if (st != HEPACC_OK) return st;
+        if (!o.counts || !o.sumw) return fail(HEPACC_ERR_INVALID_ARG, "sample %d: counts and sumw are required", i);
+        if (has_per_event(&o)) return fail(HEPACC_ERR_INVALID_ARG, "plans write no per-event outputs");
+        if (b.offsets_type != HEPACC_I64) return fail(HEPACC_ERR_DTYPE, "plans need I64 offsets");
+        if (b.kin_type != kin || b.btag_type != btag)
+            return fail(HEPACC_ERR_DTYPE, "all samples of a plan share their column types");
+        if ((b.kin_type == HEPACC_F32) != (b.btag_type == HEPACC_F32))
+            return fail(HEPACC_ERR_DTYPE, "plans take F32 btag with F32 kinematics, F16 btag with half kinematics");
+    }
+    return HEPACC_OK;
 }
 
 }  // namespace
@@ -411,26 +623,16 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     };
     hepacc_status st = make_params(cfg, p->P);
     if (st != HEPACC_OK) return drop(st);
+    st = check_plan_samples(n_samples, samples, outputs, samples[0].kin_type, samples[0].btag_type);
+    if (st != HEPACC_OK) return drop(st);
     double jets = 0, mus = 0, els = 0, events = 0;
-    p->max_events = 0;
     for (int i = 0; i < n_samples; ++i) {
         const hepacc_event_batch& b = samples[i];
-        const hepacc_chain_outputs& o = outputs[i];
-        st = check_batch(&b);
-        if (st != HEPACC_OK) return drop(st);
-        if (!o.counts || !o.sumw) return drop(fail(HEPACC_ERR_INVALID_ARG, "sample %d: counts and sumw are required", i));
-        if (has_per_event(&o)) return drop(fail(HEPACC_ERR_INVALID_ARG, "plans write no per-event outputs"));
-        if (b.offsets_type != HEPACC_I64) return drop(fail(HEPACC_ERR_DTYPE, "plans need I64 offsets"));
-        if (b.kin_type != samples[0].kin_type || b.btag_type != samples[0].btag_type)
-            return drop(fail(HEPACC_ERR_DTYPE, "all samples of a plan share their column types"));
-        if ((b.kin_type == HEPACC_F32) != (b.btag_type == HEPACC_F32))
-            return drop(fail(HEPACC_ERR_DTYPE, "plans take F32 btag with F32 kinematics, F16 btag with half kinematics"));
         const double n = static_cast<double>(b.n_events);
         jets += (b.jets_per_event > 0 ? b.jets_per_event : 6.0) * n;
         mus += (b.muons_per_event > 0 ? b.muons_per_event : 1.0) * n;
         els += (b.electrons_per_event > 0 ? b.electrons_per_event : 1.0) * n;
         events += n;
-        p->max_events = std::max<int64_t>(p->max_events, b.n_events);
     }
     if ((flags & HEPACC_PLAN_VALIDATE) || debug_checks()) {
         for (int i = 0; i < n_samples; ++i) {
@@ -438,39 +640,53 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
             if (st != HEPACC_OK) return drop(fail(st, "sample %d: %s", i, hepacc_last_error()));
         }
     }
+    p->n_samples = n_samples;
     p->kin = samples[0].kin_type;
     p->btag = samples[0].btag_type;
     const double lam_j = events > 0 ? jets / events : 6.0;
     const double lam_m = events > 0 ? mus / events : 1.0;
     const double lam_e = events > 0 ? els / events : 1.0;
     p->outs.assign(outputs, outputs + n_samples);
-    for (int i0 = 0; i0 < n_samples; i0 += kMaxSamples) {
-        BatchDesc B;
-        std::memset(&B, 0, sizeof B);
-        B.n_samples = std::min(kMaxSamples, n_samples - i0);
-        for (int j = 0; j < B.n_samples; ++j) make_sample(&samples[i0 + j], &outputs[i0 + j], B.s[j]);
-        p->launches.push_back(B);
-    }
+    p->samples.assign(samples, samples + n_samples);
+    const int flat_samples = std::min(n_samples, kMaxSamples);
 
-    // candidates: histograms in block shared memory, spread over clusters of
-    // 8 or 16 blocks, or in global memory; each with the largest block that
-    // fits
+    // candidates: the compacting kernel (global histograms) with every stage
+    // count that fits, then the walking kernel with histograms in block
+    // shared memory or spread over clusters of 8 or 16 blocks
     const size_t kes = dtype_size(p->kin), bes = dtype_size(p->btag);
     std::vector<Candidate> cands;
-    const int modes[4][3] = {{H_SMEM, 1, HEPACC_PLAN_HIST_BLOCK},
+    if (allowed & HEPACC_PLAN_HIST_GLOBAL) {
+        // block size x blocks per SM (the share of the SM's shared memory
+        // each block is laid out for) x stages
+        for (int nt : fused::kBlocks)
+            for (int bps = 1; bps * nt <= 256; ++bps)
+                for (int S = 2; S <= fused::kMaxStages; ++S) {
+                    Candidate c{};
+                    if (fused_layout(nt, S, lam_j, lam_m, lam_e, kes, bes, p->P, flat_samples, bps, c.FL) &&
+                        c.FL.cap_j >= nt * lam_j) {
+                        c.compacting = true;
+                        c.hmode = H_GLOBAL;
+                        c.cluster = 1;
+                        c.block = nt;
+                        c.blocks_per_sm = bps;
+                        c.stages = S;
+                        cands.push_back(c);
+                    }
+                }
+    }
+    const int modes[3][3] = {{H_SMEM, 1, HEPACC_PLAN_HIST_BLOCK},
                              {H_CLUSTER, 8, HEPACC_PLAN_HIST_CLUSTER8},
-                             {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16},
-                             {H_GLOBAL, 1, HEPACC_PLAN_HIST_GLOBAL}};
+                             {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16}};
     for (const auto& m : modes) {
-        // flat launches (global histograms) take the single-sample block shape
-        const int emax = m[0] == H_GLOBAL ? kMaxThreads : kMaxThreadsBatched;
-        const int bps = m[0] == H_GLOBAL ? kMinBlocks : kMinBlocksBatched;
-        for (int e = emax; e >= 64 && (allowed & m[2]); e -= 32) {
-            Candidate c;
-            if (layout_for(e, m[0], m[1], lam_j, lam_m, lam_e, kes, bes, bps, p->P, c.L)) {
+        for (int e = kMaxThreadsBatched; e >= 64 && (allowed & m[2]); e -= 32) {
+            Candidate c{};
+            if (layout_for(e, m[0], m[1], lam_j, lam_m, lam_e, kes, bes, kMinBlocksBatched, p->P, c.L)) {
+                c.compacting = false;
                 c.hmode = m[0];
                 c.cluster = m[1];
                 c.block = e;
+                c.blocks_per_sm = kMinBlocksBatched;
+                c.stages = 2;
                 cands.push_back(c);
                 break;
             }
@@ -492,10 +708,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
         }
         if (st != HEPACC_OK) return drop(st);
     }
-    p->hmode = cands[pick].hmode;
-    p->cluster = cands[pick].cluster;
-    p->block = cands[pick].block;
-    p->L = cands[pick].L;
+    p->c = cands[pick];
     if (flags & HEPACC_PLAN_GRAPH) {
         st = capture(p);
         if (st != HEPACC_OK) return drop(st);
@@ -504,25 +717,58 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     return HEPACC_OK;
 }
 
-hepacc_status hepacc_plan_run(hepacc_plan* p, hepacc_stream stream) {
+hepacc_status hepacc_plan_run(hepacc_plan* p, int32_t n_samples, const hepacc_event_batch* samples,
+                              const hepacc_chain_outputs* outputs, hepacc_stream stream) {
     if (!p) return fail(HEPACC_ERR_INVALID_ARG, "plan is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (p->exec) {
-        const cudaError_t e = cudaGraphLaunch(p->exec, s);
-        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-        return HEPACC_OK;
+    if (!samples && !outputs) {
+        if (p->exec) {
+            const cudaError_t e = cudaGraphLaunch(p->exec, s);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+            return HEPACC_OK;
+        }
+        return plan_launch(p, p->c, make_launches(p->n_samples, p->samples.data(), p->outs.data(), p->c.block), s);
     }
-    return plan_launch(p, s);
+    if (!samples || !outputs) return fail(HEPACC_ERR_INVALID_ARG, "samples and outputs go together");
+    if (n_samples != p->n_samples) return fail(HEPACC_ERR_INVALID_ARG, "the plan runs %d samples, not %d", p->n_samples, n_samples);
+    hepacc_status st = check_plan_samples(n_samples, samples, outputs, p->kin, p->btag);
+    if (st != HEPACC_OK) return st;
+    if (debug_checks()) {
+        for (int i = 0; i < n_samples; ++i) {
+            st = check_batch_offsets(&samples[i], s);
+            if (st != HEPACC_OK) return fail(st, "sample %d: %s", i, hepacc_last_error());
+        }
+    }
+    const auto launches = make_launches(n_samples, samples, outputs, p->c.block);
+    if (!p->exec) return plan_launch(p, p->c, launches, s);
+    // the captured graph, each kernel node pointed at the new descriptors
+    for (size_t i = 0; i < launches.size(); ++i) {
+        cudaKernelNodeParams kp;
+        cudaError_t e = cudaGraphKernelNodeGetParams(p->nodes[i], &kp);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel node parameters");
+        const void* args[3] = {p->c.compacting ? static_cast<const void*>(&p->c.FL) : static_cast<const void*>(&p->c.L),
+                               &p->P, &launches[i]};
+        kp.kernelParams = const_cast<void**>(args);
+        kp.extra = nullptr;
+        e = cudaGraphExecKernelNodeSetParams(p->exec, p->nodes[i], &kp);
+        if (e != cudaSuccess) return cuda_fail(e, "rebinding the plan's graph");
+    }
+    const cudaError_t e = cudaGraphLaunch(p->exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return HEPACC_OK;
 }
 
 hepacc_status hepacc_plan_describe(const hepacc_plan* p, char* buf, int32_t len) {
     if (!p || !buf || len < 1) return fail(HEPACC_ERR_INVALID_ARG, "plan and buffer are required");
-    const char* mode = p->hmode == H_SMEM ? "block" : (p->hmode == H_CLUSTER ? "cluster" : "global");
+    std::string tried;
+    for (size_t i = 0; i < p->tried.size(); ++i) tried += (i ? ", " : "") + p->tried[i];
+    const size_t nl = (p->n_samples + kMaxSamples - 1) / kMaxSamples;
+    const unsigned smem = p->c.compacting ? p->c.FL.total : p->c.L.total;
     snprintf(buf, static_cast<size_t>(len),
-             "{\"histograms\": \"%s\", \"cluster\": %d, \"block\": %d, \"smem_bytes\": %u, \"launches\": %d, "
-             "\"graph\": %s, \"candidates\": %d, \"tuned_ms\": %.4f}",
-             mode, p->cluster, p->block, p->L.total, static_cast<int>(p->launches.size()),
-             p->exec ? "true" : "false", p->n_candidates, static_cast<double>(p->tuned_ms));
+             "{\"chosen\": %s, \"smem_bytes\": %u}, \"launches\": %zu, \"graph\": %s, \"candidates\": %d, "
+             "\"tuned_ms\": %.4f, \"tried\": [%s]}",
+             describe(p->c).c_str(), smem, nl, p->exec ? "true" : "false", p->n_candidates,
+             static_cast<double>(p->tuned_ms), tried.c_str());
     return HEPACC_OK;
 }
 

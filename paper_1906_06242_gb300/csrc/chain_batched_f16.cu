@@ -9,15 +9,5 @@ hepacc_status run_batched_f16(const LaunchArgs& a) {
     return run_batched_typed<__half, __half>(a);
 }
 
-unsigned int tu_error_batched_f16(bool clear) {
-    unsigned int v = 0;
-    cudaMemcpyFromSymbol(&v, g_device_error, sizeof v);
-    if (clear && v) {
-        unsigned int z = 0;
-        cudaMemcpyToSymbol(g_device_error, &z, sizeof z);
-    }
-    return v;
-}
-
 }  // namespace chain
 }  // namespace hepacc

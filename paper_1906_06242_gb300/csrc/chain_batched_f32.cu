@@ -9,15 +9,5 @@ hepacc_status run_batched_f32(const LaunchArgs& a) {
     return run_batched_typed<float, float>(a);
 }
 
-unsigned int tu_error_batched_f32(bool clear) {
-    unsigned int v = 0;
-    cudaMemcpyFromSymbol(&v, g_device_error, sizeof v);
-    if (clear && v) {
-        unsigned int z = 0;
-        cudaMemcpyToSymbol(g_device_error, &z, sizeof z);
-    }
-    return v;
-}
-
 }  // namespace chain
 }  // namespace hepacc

@@ -1123,46 +1123,21 @@ hepacc_status launch_chain(K kernel, const LaunchArgs& a) {
     return HEPACC_OK;
 }
 
-template <typename KT>
-hepacc_status run_typed(const LaunchArgs& a) {
-    auto go = [&](auto bt, auto ot) -> hepacc_status {
-        using BT = typename decltype(bt)::type;
-        using O = typename decltype(ot)::type;
-        if (a.hmode != H_GLOBAL) return fail(HEPACC_ERR_INVALID_ARG, "single-sample launches fill global histograms");
-        if (a.debug) return launch_chain(k_chain<KT, BT, O, true, H_GLOBAL, F_SINGLE>, a);
-        return launch_chain(k_chain<KT, BT, O, false, H_GLOBAL, F_SINGLE>, a);
-    };
-    auto with_o = [&](auto bt) -> hepacc_status {
-        if (a.offsets_type == HEPACC_I32) return go(bt, Tag<int32_t>{});
-        return go(bt, Tag<int64_t>{});
-    };
-    if (a.btag_type == HEPACC_F32) return with_o(Tag<float>{});
-    return with_o(Tag<__half>{});
-}
-
-// Many samples in one launch (int64 offsets; btag float32 with float32
-// kinematics, float16 with half kinematics): shared-memory histograms walk
-// the samples in turn, global ones run the samples as one flat tile range.
+// Many samples in one launch with shared-memory histograms (int64 offsets;
+// btag float32 with float32 kinematics, float16 with half kinematics):
+// every block walks the samples in turn. Plans with global histograms run
+// the compacting kernel (fused_kernel.cuh) instead.
 template <typename KT, typename BT>
 hepacc_status run_batched_typed(const LaunchArgs& a) {
     if (a.offsets_type != HEPACC_I64) return fail(HEPACC_ERR_DTYPE, "batched launches need I64 offsets");
     if (a.hmode == H_CLUSTER) return launch_chain(k_chain<KT, BT, int64_t, false, H_CLUSTER, F_SAMPLES>, a);
     if (a.hmode == H_SMEM) return launch_chain(k_chain<KT, BT, int64_t, false, H_SMEM, F_SAMPLES>, a);
-    return launch_chain(k_chain<KT, BT, int64_t, false, H_GLOBAL, F_FLAT>, a);
+    return fail(HEPACC_ERR_INVALID_ARG, "walking launches keep their histograms in shared memory");
 }
 
-hepacc_status run_f32(const LaunchArgs& a);
-hepacc_status run_bf16(const LaunchArgs& a);
-hepacc_status run_f16(const LaunchArgs& a);
 hepacc_status run_batched_f32(const LaunchArgs& a);
 hepacc_status run_batched_bf16(const LaunchArgs& a);
 hepacc_status run_batched_f16(const LaunchArgs& a);
-unsigned int tu_error_f32(bool clear);
-unsigned int tu_error_bf16(bool clear);
-unsigned int tu_error_f16(bool clear);
-unsigned int tu_error_batched_f32(bool clear);
-unsigned int tu_error_batched_bf16(bool clear);
-unsigned int tu_error_batched_f16(bool clear);
 
 }  // namespace chain
 }  // namespace hepacc

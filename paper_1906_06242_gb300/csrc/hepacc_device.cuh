@@ -16,8 +16,25 @@ constexpr int kTile = 32;   // events per warp tile (one per lane)
 
 // Device error word of this translation unit: bit 0 = a bounded wait gave
 // up, bit 1 = a device-side input check failed. Each translation unit has its
-// own copy; hepacc_device_error() reads and clears all of them.
+// own copy, and registers a reader for it when the library is loaded, so
+// hepacc_device_error() reads and clears every copy without a list to keep.
 static __device__ unsigned int g_device_error;
+
+using ErrorWordReader = unsigned int (*)(bool clear);
+void register_error_word(ErrorWordReader reader);   // library state (api.cu)
+
+namespace {
+unsigned int read_error_word_of_unit(bool clear) {
+    unsigned int v = 0;
+    cudaMemcpyFromSymbol(&v, g_device_error, sizeof v);
+    if (clear && v) {
+        const unsigned int z = 0;
+        cudaMemcpyToSymbol(g_device_error, &z, sizeof z);
+    }
+    return v;
+}
+const bool g_error_word_registered = (register_error_word(&read_error_word_of_unit), true);
+}  // namespace
 
 constexpr unsigned int kErrTimeout = 1u;
 constexpr unsigned int kErrCheck = 2u;

@@ -29,10 +29,16 @@ DeviceInfo device_info();
 
 // Debug checks before chain launches (environment variable HEPACC_DEBUG set
 // and not 0), and the offsets check they run: a kernel over the offsets,
-// then a wait for it; HEPACC_ERR_DEVICE_CHECK when offsets[0] < 0 or the
-// offsets decrease.
+// then a wait for it; HEPACC_ERR_DEVICE_CHECK when offsets[0] < 0, the
+// offsets decrease, or offsets[n] > content_len.
 bool debug_checks();
-hepacc_status check_offsets_nondecreasing(const void* offsets, hepacc_dtype ot, int64_t n, cudaStream_t s);
+
+// Readers of the device error words: every translation unit that includes
+// the device header registers one (hepacc_device.cuh); hepacc_device_error()
+// calls them all.
+using ErrorWordReader = unsigned int (*)(bool clear);
+void register_error_word(ErrorWordReader reader);
+hepacc_status check_offsets(const void* offsets, hepacc_dtype ot, int64_t n, int64_t content_len, cudaStream_t s);
 
 inline bool is_float_type(hepacc_dtype t) { return t == HEPACC_F32 || t == HEPACC_F16 || t == HEPACC_BF16; }
 inline bool is_offsets_type(hepacc_dtype t) { return t == HEPACC_I32 || t == HEPACC_I64; }

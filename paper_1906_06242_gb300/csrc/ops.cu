@@ -23,15 +23,6 @@ bool debug_checks() {
     return on;
 }
 
-unsigned int tu_error_ops(bool clear) {
-    unsigned int v = 0;
-    cudaMemcpyFromSymbol(&v, g_device_error, sizeof v);
-    if (clear && v) {
-        unsigned int z = 0;
-        cudaMemcpyToSymbol(g_device_error, &z, sizeof z);
-    }
-    return v;
-}
 
 namespace {
 
@@ -1103,13 +1094,14 @@ __global__ void k_validate(const OffT* off, int64_t n, int64_t m, unsigned long 
 }
 
 // Offsets check that reports through the device error word: bit 1 when
-// offsets[0] < 0 or offsets decrease anywhere.
+// offsets[0] < 0, the offsets decrease anywhere, or offsets[n] > m (the
+// content length).
 template <typename OffT>
-__global__ void k_check_offsets(const OffT* off, int64_t n) {
+__global__ void k_check_offsets(const OffT* off, int64_t n, int64_t m) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t a = ldoff(off, i), b = ldoff(off, i + 1);
-        if (b < a || (i == 0 && a < 0)) atomicOr(&g_device_error, kErrCheck);
+        if (b < a || (i == 0 && a < 0) || (i + 1 == n && b > m)) atomicOr(&g_device_error, kErrCheck);
     }
 }
 
@@ -1665,12 +1657,12 @@ namespace hepacc {
 // Launches the offsets check, waits for it and reads (and clears) the check
 // bit of this translation unit's error word: HEPACC_ERR_DEVICE_CHECK if the
 // offsets are negative at the start or decrease.
-hepacc_status check_offsets_nondecreasing(const void* offsets, hepacc_dtype ot, int64_t n, cudaStream_t s) {
+hepacc_status check_offsets(const void* offsets, hepacc_dtype ot, int64_t n, int64_t content_len, cudaStream_t s) {
     if (n <= 0) return HEPACC_OK;
     if (!offsets) return fail(HEPACC_ERR_INVALID_ARG, "offsets are required");
     hepacc_status st = with_offsets_type(ot, [&](auto ot_tag) -> hepacc_status {
         using O = typename decltype(ot_tag)::type;
-        k_check_offsets<O><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const O*>(offsets), n);
+        k_check_offsets<O><<<flat_grid(n), kBlock, 0, s>>>(static_cast<const O*>(offsets), n, content_len);
         HEPACC_CHECK_LAUNCH("offsets check launch");
         return HEPACC_OK;
     });
@@ -1682,7 +1674,7 @@ hepacc_status check_offsets_nondecreasing(const void* offsets, hepacc_dtype ot, 
     if (v & kErrCheck) {
         const unsigned int keep = v & ~kErrCheck;
         cudaMemcpyToSymbol(g_device_error, &keep, sizeof keep);
-        return fail(HEPACC_ERR_DEVICE_CHECK, "offsets are negative at the start or decrease");
+        return fail(HEPACC_ERR_DEVICE_CHECK, "offsets are negative at the start, decrease, or end past the content");
     }
     return HEPACC_OK;
 }

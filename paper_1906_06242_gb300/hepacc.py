@@ -70,7 +70,8 @@ def load(build_if_missing: bool = True):
         getattr(L, name).restype = ctypes.c_int
     L.hepacc_plan_destroy.restype = None
     L.hepacc_plan_destroy.argtypes = [ctypes.c_void_p]
-    L.hepacc_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.hepacc_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]
     L.hepacc_plan_describe.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]
     _lib = L
     return L
@@ -353,7 +354,8 @@ class EventBatchC(ctypes.Structure):
                 ("el_pt", _c_void_p), ("el_eta", _c_void_p), ("el_phi", _c_void_p), ("el_iso", _c_void_p),
                 ("el_tight", _c_void_p),
                 ("weight", _c_void_p), ("jets_per_event", ctypes.c_float),
-                ("muons_per_event", ctypes.c_float), ("electrons_per_event", ctypes.c_float)]
+                ("muons_per_event", ctypes.c_float), ("electrons_per_event", ctypes.c_float),
+                ("jet_len", ctypes.c_int64), ("mu_len", ctypes.c_int64), ("el_len", ctypes.c_int64)]
 
 
 class ChainConfigC(ctypes.Structure):
@@ -429,6 +431,9 @@ class DeviceBatch:
         c.jets_per_event = self.cols["jet_pt"].numel() / n
         c.muons_per_event = self.cols["mu_pt"].numel() / n
         c.electrons_per_event = self.cols["el_pt"].numel() / n
+        c.jet_len = self.cols["jet_pt"].numel()
+        c.mu_len = self.cols["mu_pt"].numel()
+        c.el_len = self.cols["el_pt"].numel()
         self._c = c
         return c
 
@@ -537,10 +542,26 @@ class Plan:
         self.cfg = cfg
 
     def run(self, stream=None):
-        _check(load().hepacc_plan_run(self._h, _stream(stream)))
+        """Run the samples and outputs the plan was created with."""
+        _check(load().hepacc_plan_run(self._h, 0, None, None, _stream(stream)))
+
+    def run_batch(self, batches, outputs, stream=None, _structs=None):
+        """Run the plan's configuration (and graph) over another batch of as
+        many samples: ``batches[i]`` adds to ``outputs[i]``. The tensors must
+        stay alive until the run is done; the returned structs can be passed
+        back as ``_structs`` to skip rebuilding them."""
+        if _structs is None:
+            if len(batches) != len(outputs):
+                raise ValueError("one output per sample")
+            n = len(batches)
+            _structs = (n, (EventBatchC * n)(*[b.c_struct() for b in batches]),
+                        (ChainOutputsC * n)(*[o.c_struct() for o in outputs]))
+        n, bs, os_ = _structs
+        _check(load().hepacc_plan_run(self._h, n, bs, os_, _stream(stream)))
+        return _structs
 
     def describe(self) -> dict:
-        buf = ctypes.create_string_buffer(512)
+        buf = ctypes.create_string_buffer(16384)
         _check(load().hepacc_plan_describe(self._h, buf, len(buf)))
         return json.loads(buf.value.decode())
 

@@ -70,9 +70,9 @@ def test_plan_placements_one_variation(H, orc, placement):
     samples = [synth.generate(n, 40 + i, offset_dtype=np.int64) for i, n in enumerate([9_001, 0, 20_011, 313, 1])]
     res, desc = run_plan(H, samples, [0], flags=placement)
     want = {BLOCK: "block", CL8: "cluster", CL16: "cluster", GLOBAL: "global"}[placement]
-    assert desc["histograms"] == want
+    assert desc["chosen"]["histograms"] == want
     if placement in (CL8, CL16):
-        assert desc["cluster"] == placement
+        assert desc["chosen"]["cluster"] == placement
     check_samples(orc, samples, [0], res)
 
 
