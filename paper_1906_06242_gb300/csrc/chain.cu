@@ -249,8 +249,8 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
     L.bars = region(at, 8 * fused::kMaxStages + 6 * 8);
     L.edges = region(at, static_cast<size_t>(P.n_edges) * 4);
     L.scales = region(at, static_cast<size_t>(P.n_var) * 4);
-    L.samples = region(at, static_cast<size_t>(flat_samples) * sizeof(SampleDesc));
-    L.misc = region(at, (4 + 32) * 4);
+    L.samples = region(at, static_cast<size_t>(std::max(flat_samples, 1)) * sizeof(SampleDesc));
+    L.misc = region(at, fused::kMiscWords * 4 + sizeof(L.col));   // counter, warp totals, column specs
     const DeviceInfo di = device_info();
     const size_t limit =
         std::min(static_cast<size_t>(di.smem_per_sm / blocks_per_sm - di.smem_reserved), static_cast<size_t>(di.smem_optin));

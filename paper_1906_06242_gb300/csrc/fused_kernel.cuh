@@ -47,6 +47,8 @@ using namespace chain;   // column indices J_PT ... E_TIGHT
 
 constexpr int kMaxStages = 4;
 constexpr int kHdrBytes = 96;   // stage header: spans (3 x int64), column offsets (15 x u32), staged flag
+constexpr int kMiscWords = 36;  // misc region: counter word, three spare words, 32 warp totals; the
+                                // column specifications follow
 
 // Shared-memory layout of a block (byte offsets into dynamic shared memory).
 struct FLayout {
@@ -64,7 +66,7 @@ struct FLayout {
     // buffered jets
     uint32_t j_pt, j_eta, j_phi, j_m, j_bt, j_c, j_s;   // float
     uint32_t j_acc;         // uint8
-    uint32_t misc;          // counter word (events << 16 | jets), warp scan scratch
+    uint32_t misc;          // counter word (events << 16 | jets), warp scan scratch, column specifications
     uint32_t total;
 };
 
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t* s_ws = s_cnt + 4;   // warp totals of a block scan
     const uint32_t smem0 = smem_addr(smem);
     SampleDesc* s_samples = reinterpret_cast<SampleDesc*>(smem + L.samples);
+    ColSpec* s_cols = reinterpret_cast<ColSpec*>(smem + L.misc + kMiscWords * 4);
 
     // buffer arrays
     int32_t* b_e = reinterpret_cast<int32_t*>(smem + L.b_e);
@@ -401,10 +404,15 @@ __global__ void __launch_bounds__(NT, 1)
 
     for (int i = tid; i < P.n_edges; i += NT) s_edges[i] = P.edges[i];
     for (int i = tid; i < P.n_var; i += NT) s_scales[i] = P.scales[i];
-    if constexpr (FLAT) {
-        const int words = B.n_samples * static_cast<int>(sizeof(SampleDesc) / 8);
+    // the samples' descriptors and the column specifications in shared
+    // memory: lanes read them at different indices, which the constant bank
+    // holding kernel parameters would serialise
+    {
+        const int words = (FLAT ? B.n_samples : 1) * static_cast<int>(sizeof(SampleDesc) / 8);
         for (int i = tid; i < words; i += NT)
             reinterpret_cast<uint64_t*>(s_samples)[i] = reinterpret_cast<const uint64_t*>(&B.s[0])[i];
+        for (int i = tid; i < static_cast<int>(sizeof(L.col) / 8); i += NT)
+            reinterpret_cast<uint64_t*>(s_cols)[i] = reinterpret_cast<const uint64_t*>(&L.col[0])[i];
     }
     if (tid == 0) {
         for (int b = 0; b < S; ++b) mbar_init(smem_addr(bars + b), 1);
@@ -413,6 +421,8 @@ __global__ void __launch_bounds__(NT, 1)
     }
     __syncthreads();
 
+    // a sample's descriptor (uniform reads: kernel parameters for a single
+    // sample; the lanes' indexed reads in issue() use the shared copy)
     auto SD = [&](int s) -> const SampleDesc& {
         if constexpr (FLAT)
             return s_samples[s];
@@ -465,12 +475,12 @@ __global__ void __launch_bounds__(NT, 1)
         uint32_t bytes = 0;
         uintptr_t a16 = 0;
         bool fits_c = true;
-        const int coll = lane < NC ? static_cast<int>(L.col[lane].coll) : 0;
+        const int coll = lane < NC ? static_cast<int>(s_cols[lane].coll) : 0;
         const int64_t S0 = __shfl_sync(0xffffffffu, sp, coll);
         const int64_t T0 = __shfl_sync(0xffffffffu, sp, 3 + coll);
         if (lane < NC) {
-            const ColSpec& cs = L.col[lane];
-            const uintptr_t cb = reinterpret_cast<uintptr_t>(sd.col[lane]);
+            const ColSpec& cs = s_cols[lane];
+            const uintptr_t cb = reinterpret_cast<uintptr_t>(s_samples[ts].col[lane]);
             const uintptr_t a = cb + static_cast<uintptr_t>(S0) * cs.es;
             const uintptr_t z = cb + static_cast<uintptr_t>(T0) * cs.es;
             a16 = a & ~uintptr_t(15);
@@ -484,18 +494,16 @@ __global__ void __launch_bounds__(NT, 1)
         for (int d = 16; d >= 1; d >>= 1) total += __shfl_xor_sync(0xffffffffu, total, d);
         if (lane < 3) hdr[lane] = sp;
         if (lane == 0) hoff[NC] = fits ? 1u : 0u;
+        // one proxy fence for the warp: the stage's earlier generic reads
+        // are ordered before the copies that overwrite it
         __syncwarp();
+        fence_proxy_async_smem();
         const uint32_t bar = smem_addr(bars + b);
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, fits ? total : 0u);
-        }
+        if (lane == 0) mbar_arrive_expect_tx(bar, fits ? total : 0u);
         __syncwarp();
-        if (fits && lane < NC && bytes > 0) {
-            fence_proxy_async_smem();
-            bulk_g2s(smem0 + b * L.stage_bytes + kHdrBytes + L.col[lane].soff, reinterpret_cast<const void*>(a16),
+        if (fits && lane < NC && bytes > 0)
+            bulk_g2s(smem0 + b * L.stage_bytes + kHdrBytes + s_cols[lane].soff, reinterpret_cast<const void*>(a16),
                      bytes, bar);
-        }
     };
     // this thread's offsets and weight in tile t
     auto own_offsets = [&](int64_t t, int64_t (&os)[3], int64_t (&ot)[3], float& w) {
@@ -598,13 +606,18 @@ __global__ void __launch_bounds__(NT, 1)
     int maxj = 0, maxe = 0;   // most jets / events one tile appended so far (same in every thread)
     uint32_t last_cnt = 0;
     int64_t it = 0;
+    // the tile's stage, the stage refilled at its start (the previous
+    // tile's), and the phase parity of each stage's barrier: advanced once
+    // per tile, so that the loop does no integer division
+    int b = 0, bprev = S - 1;
+    uint32_t parbits = 0u;
     for (int64_t tile = t0; tile < ntiles; tile += G, ++it) {
-        const int b = static_cast<int>(it % S);
         const int64_t next = tile + G;
         int64_t ns_[3] = {0, 0, 0}, nt_[3] = {0, 0, 0};
         float nw_ = 0.0f;
         if (next < ntiles) own_offsets(next, ns_, nt_, nw_);
-        const bool ok = mbar_wait_bounded(smem_addr(bars + b), static_cast<uint32_t>((it / S) & 1));
+        const bool ok = mbar_wait_bounded(smem_addr(bars + b), (parbits >> b) & 1u);
+        parbits ^= 1u << b;
         // every thread is done with the previous tile: its stage is free and
         // the buffer counter is settled
         if (!__syncthreads_and(ok)) {
@@ -621,7 +634,7 @@ __global__ void __launch_bounds__(NT, 1)
             if (warp == 0) {
                 const int64_t tn = tile + (S - 1) * G;
                 if (tn < ntiles) {
-                    issue(static_cast<int>((it + S - 1) % S), tn, sp_next);
+                    issue(bprev, tn, sp_next);
                     if (tn + G < ntiles) sp_next = load_span(tn + G);
                 }
             }
@@ -838,15 +851,19 @@ __global__ void __launch_bounds__(NT, 1)
             ct_[c] = nt_[c];
         }
         cw_ = nw_;
+        bprev = b;
+        b = b + 1 == S ? 0 : b + 1;
     }
     if (stop) {
         // a bounded wait gave up (error word set): let the copies already
         // issued land before the block exits, then leave the rest undone
-        for (int64_t j = 0; j < S - 1; ++j) {
+        // (the failed tile's parity bit was already flipped)
+        for (int j = 0; j < S - 1; ++j) {
             const int64_t tj = t0 + (it + j) * G;
             if (tj >= ntiles) break;
-            if (tid == 0) mbar_wait_bounded(smem_addr(bars + static_cast<int>((it + j) % S)),
-                                            static_cast<uint32_t>(((it + j) / S) & 1));
+            const int sb = b + j < S ? b + j : b + j - S;
+            const uint32_t par = ((parbits >> sb) & 1u) ^ (j == 0 ? 1u : 0u);
+            if (tid == 0) mbar_wait_bounded(smem_addr(bars + sb), par);
         }
         return;
     }
