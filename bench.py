@@ -311,7 +311,8 @@ def main():
         d2h = sum(t.numel() * t.element_size() for t in res_host)
         dev_bufs = {k: torch.empty_like(t, device="cuda") for k, t in pinned.items()}
         db2 = H.DeviceBatch(batch.n_events, {k: dev_bufs["off_" + k] for k in ("jet", "mu", "el")},
-                            {name: dev_bufs[name] for name in H.COLUMNS}, dev_bufs["weight"])
+                            {name: dev_bufs[name] for name in H.COLUMNS}, dev_bufs["weight"],
+                            objects={k: int(v[-1] - v[0]) for k, v in batch.offsets.items()})
         out2 = H.ChainOutputs(cfg, batch.n_events, per_event=False, sumw2=True)
         s2 = (db2.c_struct(), cfg.c_struct(), out2.c_struct())
 

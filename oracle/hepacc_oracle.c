@@ -100,19 +100,30 @@ static int on(const uint8_t *mask, int64_t i) { return mask == NULL || mask[i] !
  * Generic kernels (Section III)
  * ------------------------------------------------------------------------- */
 
-/* sum_in_offsets over floating content (Listing 1): for every event with
- * mask_rows set, out[ev] += x[i] for each element i of the event with
- * mask_content set, in element order, in FP32. Other events are untouched. */
+/* The FP32 sum of the masked-in elements of x in [lo, hi), one addition at
+ * a time in element order, starting from acc. */
+static float fsum_masked(const void *x, int xt, int64_t lo, int64_t hi, const uint8_t *mask, float acc)
+{
+    for (int64_t i = lo; i < hi; i++)
+        if (on(mask, i))
+            acc = acc + get_f(x, xt, i);
+    return acc;
+}
+
+/* sum_in_offsets over floating content (Section III): event ev owns the
+ * elements [off[ev], off[ev+1]); a selected event (mask_rows) adds the FP32
+ * sum of its masked-in elements (mask_content), in element order, to the
+ * value already in out[ev]; other events keep theirs. One pass over the
+ * events, the end of one event's range being the start of the next. */
 void oracle_sum_in_offsets_f(const void *x, int xt, const void *off, int ot, int64_t n,
                              const uint8_t *mask_rows, const uint8_t *mask_content, float *out)
 {
+    int64_t lo = n > 0 ? get_off(off, ot, 0) : 0;
     for (int64_t ev = 0; ev < n; ev++) {
-        if (!on(mask_rows, ev))
-            continue;
-        int64_t i0 = get_off(off, ot, ev), i1 = get_off(off, ot, ev + 1);
-        for (int64_t i = i0; i < i1; i++)
-            if (on(mask_content, i))
-                out[ev] += get_f(x, xt, i);
+        const int64_t hi = get_off(off, ot, ev + 1);
+        if (on(mask_rows, ev))
+            out[ev] = fsum_masked(x, xt, lo, hi, mask_content, out[ev]);
+        lo = hi;
     }
 }
 

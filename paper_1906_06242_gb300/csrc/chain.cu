@@ -299,9 +299,13 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
 bool single_config(double lam_j, double lam_m, double lam_e, size_t kes, size_t bes, const ChainParams& P,
                    fused::FLayout& L, int& NT) {
     NT = fused::kDebugBlock;
-    const int bps = 2;
-    if (fused_layout(NT, 2, lam_j, lam_m, lam_e, kes, bes, P, 0, bps, L)) return true;
-    return fused_layout(NT, 2, lam_j, lam_m, lam_e, kes, bes, P, 0, 1, L);
+    // objects per event so dense that no stage fits: smaller stages (the
+    // tiles that do not fit one are read from global memory)
+    for (double f = 1.0; f >= 1.0 / 64; f *= 0.5) {
+        if (fused_layout(NT, 2, lam_j * f, lam_m * f, lam_e * f, kes, bes, P, 0, 2, L)) return true;
+        if (fused_layout(NT, 2, lam_j * f, lam_m * f, lam_e * f, kes, bes, P, 0, 1, L)) return true;
+    }
+    return fused_layout(NT, 2, 1.0, 0.25, 0.25, kes, bes, P, 0, 1, L);
 }
 
 hepacc_status dispatch_fused(hepacc_dtype kin, const fused::FusedArgs& a) {
@@ -643,9 +647,9 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     p->n_samples = n_samples;
     p->kin = samples[0].kin_type;
     p->btag = samples[0].btag_type;
-    const double lam_j = events > 0 ? jets / events : 6.0;
-    const double lam_m = events > 0 ? mus / events : 1.0;
-    const double lam_e = events > 0 ? els / events : 1.0;
+    const double lam_j0 = events > 0 ? jets / events : 6.0;
+    const double lam_m0 = events > 0 ? mus / events : 1.0;
+    const double lam_e0 = events > 0 ? els / events : 1.0;
     p->outs.assign(outputs, outputs + n_samples);
     p->samples.assign(samples, samples + n_samples);
     const int flat_samples = std::min(n_samples, kMaxSamples);
@@ -655,6 +659,10 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     // shared memory or spread over clusters of 8 or 16 blocks
     const size_t kes = dtype_size(p->kin), bes = dtype_size(p->btag);
     std::vector<Candidate> cands;
+    // objects per event so dense that nothing fits: smaller stages (tiles
+    // that do not fit one are read from global memory)
+    for (double f = 1.0; cands.empty() && f >= 1.0 / 64; f *= 0.5) {
+    const double lam_j = lam_j0 * f, lam_m = lam_m0 * f, lam_e = lam_e0 * f;
     if (allowed & HEPACC_PLAN_HIST_GLOBAL) {
         // block size x blocks per SM (the share of the SM's shared memory
         // each block is laid out for) x stages
@@ -691,6 +699,7 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
                 break;
             }
         }
+    }
     }
     if (cands.empty()) return drop(fail(HEPACC_ERR_INVALID_ARG, "no chain layout fits in shared memory"));
     p->n_candidates = static_cast<int>(cands.size());

@@ -380,11 +380,12 @@ class DeviceBatch:
     """Device-resident columns of one sample (torch tensors) and the C struct
     pointing at them."""
 
-    def __init__(self, n_events, offsets, cols, weight):
+    def __init__(self, n_events, offsets, cols, weight, objects=None):
         self.n_events = int(n_events)
         self.offsets = offsets      # dict jet/mu/el -> tensor
         self.cols = cols            # dict name -> tensor
         self.weight = weight
+        self._objects = objects     # dict jet/mu/el -> objects in these events (None: read from the offsets)
         self._c = None
 
     @classmethod
@@ -407,7 +408,19 @@ class DeviceBatch:
             a = batch.cols[name]
             fmt = btag_fmt if name == "jet_btag" else kin_fmt
             cols[name] = up(a, fmt)
-        return cls(batch.n_events, offsets, cols, up(batch.weight))
+        objects = {k: int(v[-1] - v[0]) if len(v) else 0 for k, v in batch.offsets.items()}
+        return cls(batch.n_events, offsets, cols, up(batch.weight), objects=objects)
+
+    def objects(self) -> dict:
+        """Objects per collection in this batch's events (offsets[n] -
+        offsets[0]; a slice of a larger batch shares its columns): as given
+        at construction, else read once from the device offsets."""
+        if getattr(self, "_objects", None) is None:
+            if self.n_events == 0:
+                self._objects = {k: 0 for k in self.offsets}
+            else:
+                self._objects = {k: int((v[-1] - v[0]).item()) for k, v in self.offsets.items()}
+        return self._objects
 
     def nbytes_read(self) -> int:
         """Bytes of every array the chain reads: offsets, the 15 columns, weight."""
@@ -428,9 +441,10 @@ class DeviceBatch:
             setattr(c, name, _addr(self.cols[name]))
         c.weight = _addr(self.weight)
         n = max(1, self.n_events)
-        c.jets_per_event = self.cols["jet_pt"].numel() / n
-        c.muons_per_event = self.cols["mu_pt"].numel() / n
-        c.electrons_per_event = self.cols["el_pt"].numel() / n
+        objs = self.objects()
+        c.jets_per_event = objs["jet"] / n
+        c.muons_per_event = objs["mu"] / n
+        c.electrons_per_event = objs["el"] / n
         c.jet_len = self.cols["jet_pt"].numel()
         c.mu_len = self.cols["mu_pt"].numel()
         c.el_len = self.cols["el_pt"].numel()

@@ -105,8 +105,9 @@ class StreamedChain:
             buf = self.bufs[i % len(self.bufs)]
             v = {k: buf[k][:t.numel()] for k, t in p.items()}
             n = p["weight"].numel()
+            objects = {c: int(p["off_" + c][-1]) if n else 0 for c in COLLECTIONS}   # host offsets rebased to 0
             db = H.DeviceBatch(n, {c: v["off_" + c] for c in COLLECTIONS}, {name: v[name] for name in H.COLUMNS},
-                               v["weight"])
+                               v["weight"], objects=objects)
             self.views.append((v, db, (db.c_struct(), cfg.c_struct(), out.c_struct())))
         self.copy_stream = torch.cuda.Stream(device=device)
         self.copied = [torch.cuda.Event() for _ in self.bufs]

@@ -165,3 +165,12 @@ def test_chain_full_size_plain_10m(H, orc):
     stats = CC.compare_hists(g["counts"], g["sumw"], g["sumw2"], o, batch.weight, o["nbins"], o["edges"])
     print("plain_10m", stats)
     assert H.device_error() == 0
+
+
+def test_chain_too_dense_for_any_stage(H, orc):
+    # 60 jets and 6 muons per event: a stage sized for that density does not
+    # fit in shared memory; the call lays out smaller stages and the tiles
+    # that do not fit them are read from global memory (per-event outputs
+    # and histograms, against the oracle)
+    batch = synth.generate(1_501, 91, lam_jet=60.0, lam_mu=6.0)
+    check(H, orc, batch, [0, 5])

@@ -139,3 +139,35 @@ def test_plan_rejects_bad_samples(H):
     with pytest.raises(H.HepaccError):   # unknown flag
         H.hepacc_plan_create(cfg, [db], [H.ChainOutputs(cfg, 100)], flags=1 << 10)
     assert H.device_error() == 0
+
+
+@pytest.mark.parametrize("flags", [1 | 2, GLOBAL | 2, CL16 | 2, GLOBAL])
+def test_plan_reused_over_batches(H, orc, flags):
+    # one plan (tuned and captured on the first set) run over three sets of
+    # the same number of samples and column types, with other event counts
+    # and contents (Section II: the cache is processed batch after batch);
+    # each run equals the oracle on its own set
+    shifts = synth.variation_shifts(5)
+    cfg = config(H, shifts)
+    sets = [[synth.generate(n, 300 + 10 * b + i, offset_dtype=np.int64) for i, n in enumerate(sizes)]
+            for b, sizes in enumerate([(20_011, 3_001, 512), (4_003, 25_013, 1), (9_001, 0, 17_077)])]
+    dbs = [[H.DeviceBatch.from_host(s) for s in st] for st in sets]
+    outs = [[H.ChainOutputs(cfg, s.n_events) for s in st] for st in sets]
+    plan = H.hepacc_plan_create(cfg, dbs[0], outs[0], flags=flags)
+    plan.run()
+    for b in (1, 2):
+        plan.run_batch(dbs[b], outs[b])
+    torch.cuda.synchronize()
+    desc = plan.describe()
+    # a batch of another sample count or column type is refused
+    with pytest.raises(H.HepaccError):
+        plan.run_batch(dbs[1][:2], outs[1][:2])
+    bf = [H.DeviceBatch.from_host(synth.reduced_precision(s, "bf16")) for s in sets[1]]
+    with pytest.raises(H.HepaccError):
+        plan.run_batch(bf, outs[1])
+    plan.close()
+    assert H.device_error() == 0
+    print(flags, desc["chosen"])
+    for st, os_ in zip(sets, outs):
+        res = [(o.counts.cpu().numpy().view(np.uint64), o.sumw.cpu().numpy(), o.sumw2.cpu().numpy()) for o in os_]
+        check_samples(orc, st, shifts, res)

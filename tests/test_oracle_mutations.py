@@ -15,7 +15,8 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 MUTATIONS = [
     ("dphi wrap sign", "dphi = dphi - OR_TWO_PI_F;", "dphi = dphi + OR_TWO_PI_F;"),
     ("dr2 operand", "float a = deta * deta;", "float a = deta * dphi;"),
-    ("sum assigns", "out[ev] += get_f(x, xt, i);", "out[ev] = get_f(x, xt, i);"),
+    ("sum assigns", "acc = acc + get_f(x, xt, i);", "acc = get_f(x, xt, i);"),
+    ("sum range cursor not advanced", "        lo = hi;\n", "\n"),
     ("max tie keeps last", "(want_max ? v > best : v < best)", "(want_max ? v >= best : v <= best)"),
     ("pz uses cosh", "v.pz = pt * sinh(eta);", "v.pz = pt * cosh(eta);"),
     ("mass sign", "double m2 = v.e * v.e - (", "double m2 = v.e * v.e + ("),
@@ -42,6 +43,14 @@ MUTATIONS = [
     ("nd NaN goes to underflow", "skip = 1;\n                break;", "b = 0;"),
     ("nd cell order reversed", "for (int d = 0; d < ndim; d++) {", "for (int d = ndim - 1; d >= 0; d--) {"),
     ("mass clamp maps NaN to 0", "return sqrt(m2 < 0.0 ? 0.0 : m2);", "return sqrt(m2 > 0.0 ? m2 : 0.0);"),
+    ("scale adds", "out[i] = get_f(x, xt, i) * s;", "out[i] = get_f(x, xt, i) + s;"),
+    ("scale reads the next element", "out[i] = get_f(x, xt, i) * s;", "out[i] = get_f(x, xt, i + 1 < m ? i + 1 : i) * s;"),
+    ("scale rounds toward zero", "out[i] = get_f(x, xt, i) * s;",
+     "{ double d = (double)get_f(x, xt, i) * s; float f = (float)d; out[i] = fabs((double)f) > fabs(d) ? "
+     "nextafterf(f, 0.0f) : f; }"),
+    ("pair index at the count allowed", "a >= i1 - i0 || b >= i1 - i0", "a > i1 - i0 || b > i1 - i0"),
+    ("pair index not rebased", "a += i0;\n        b += i0;", "a += 0;\n        b += 0;"),
+    ("pair negative index allowed", "if (a < 0 || b < 0 ||", "if ("),
 ]
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

@@ -840,3 +840,77 @@ def test_get_bin_contents_interpolation(orc):
     one = orc.get_bin_contents(np.array([-1, 0.5, 3], np.float32), np.array([0, 1], np.float32),
                                np.array([5, 6, 7], np.float32), interpolate=True)
     np.testing.assert_array_equal(one, [6, 6, 6])
+
+
+# ---------------------------------------------------------------------------
+# jet-pt scale variation: one binary32 product, round to nearest even
+# ---------------------------------------------------------------------------
+
+def test_scale_binary32_products_by_hand(orc):
+    # exact products and hand-rounded ones (ulp of [1, 2) is 2^-23):
+    #  3 * 0.5 = 1.5 exactly;
+    #  (1 + 2^-12)^2 = 1 + 2^-11 + 2^-24: half an ulp above 1 + 2^-11, a tie,
+    #    to even: 1 + 2^-11 (its last mantissa bit is 0);
+    #  (1 + 3 2^-12)^2 = 1 + 3 2^-11 + 4.5 2^-23: a tie between 4 and 5 ulps
+    #    above 1 + 3 2^-11, to even: + 4 ulps = + 2^-21;
+    #  (1 + 2^-23) * 1.75 = 1.75 + 1.75 2^-23: 1.75 ulps, to nearest: + 2 ulps;
+    #  2^127 * 2 overflows to +inf; -0 * 2 = -0; inf * 2 = inf; NaN stays NaN.
+    x = np.array([3.0, 1 + 2 ** -12, 1 + 3 * 2 ** -12, 1 + 2 ** -23, 2.0 ** 127, -0.0, np.inf, np.nan],
+                 dtype=np.float32)
+    s = [0.5, 1 + 2 ** -12, 1 + 3 * 2 ** -12, 1.75, 2.0, 2.0, 2.0, 2.0]
+    want = [1.5, 1 + 2 ** -11, 1 + 3 * 2 ** -11 + 2 ** -21, 1.75 + 2 ** -22, np.inf, -0.0, np.inf, np.nan]
+    for xi, si, wi in zip(x, s, want):
+        got = orc.scale(np.array([xi], dtype=np.float32), float(si))[0]
+        if np.isnan(wi):
+            assert np.isnan(got)
+        else:
+            assert got == np.float32(wi), (xi, si, got, wi)
+            assert np.signbit(got) == np.signbit(np.float32(wi))
+
+
+def test_scale_half_inputs_widen_exactly(orc):
+    # binary16 0x3E00 = 1.5 and bfloat16 0x3FC0 = 1.5 (the upper half of the
+    # binary32 pattern 0x3FC00000); 1.5 * 2 = 3 and 1.5 * 3 = 4.5 exactly
+    f16 = np.array([0x3E00, 0x3C00, 0x7C00], dtype=np.uint16)   # 1.5, 1.0, +inf
+    got = orc.scale(f16, 2.0, fmt="f16")
+    assert got[0] == 3.0 and got[1] == 2.0 and np.isinf(got[2])
+    bf = np.array([0x3FC0, 0xBF80], dtype=np.uint16)             # 1.5, -1.0
+    got = orc.scale(bf, 3.0, fmt="bf16")
+    assert got[0] == 4.5 and got[1] == -3.0
+    # element by element: the i-th output comes from the i-th input only
+    x = np.arange(1, 8, dtype=np.float32)
+    np.testing.assert_array_equal(orc.scale(x, 2.0), 2.0 * np.arange(1, 8))
+
+
+# ---------------------------------------------------------------------------
+# pair mass: local indices inside sliced events, NaN outside
+# ---------------------------------------------------------------------------
+
+def test_pair_mass_local_indices_and_sliced_offsets(orc):
+    # content starts with 5 elements that belong to no event (offsets[0] = 5,
+    # a slice of a larger batch); events: [0] two massless objects back to
+    # back (m = 2 pt = 80), [1] three objects, pair (2, 0) massless at right
+    # angles (m^2 = 2 pt1 pt2 (1 - cos 90deg) = 1800), [2] one object, index 1
+    # is its count: NaN, [3] index -1: NaN, [4] an object paired with itself
+    # (twice its mass: 10)
+    junk = [999.0] * 5
+    pt = np.array(junk + [40, 40, 30, 7, 30, 12, 13, 10], dtype=np.float32)
+    eta = np.array(junk + [0, 0, 0, 2, 0, 0, 0, 0.3], dtype=np.float32)
+    phi = np.array(junk + [0, math.pi, 0, 1, math.pi / 2, 0, 0, 1.0], dtype=np.float32)
+    m = np.array(junk + [0, 0, 0, 3, 0, 1, 1, 5], dtype=np.float32)
+    off = np.array([5, 7, 10, 11, 12, 13], dtype=np.int64)
+    ia = [0, 2, 1, -1, 0]
+    ib = [1, 0, 0, 0, 0]
+    got = orc.pair_mass(pt, eta, phi, m, off, ia, ib)
+    assert abs(got[0] - 80.0) <= 1e-9 * 80
+    assert abs(got[1] - math.sqrt(1800.0)) <= 1e-6 * math.sqrt(1800.0)
+    assert np.isnan(got[2]) and np.isnan(got[3])
+    assert abs(got[4] - 10.0) <= 1e-9 * 10
+    # int32 offsets give the same
+    got32 = orc.pair_mass(pt, eta, phi, m, off.astype(np.int32), ia, ib)
+    np.testing.assert_array_equal(np.isnan(got32), np.isnan(got))
+    ok = ~np.isnan(got)
+    np.testing.assert_array_equal(got32[ok], got[ok])
+    # rows with mask_rows unset keep their value (NaN here)
+    masked = orc.pair_mass(pt, eta, phi, m, off, ia, ib, mask_rows=np.array([0, 1, 1, 1, 1], dtype=np.uint8))
+    assert np.isnan(masked[0]) and masked[1] == got[1]
