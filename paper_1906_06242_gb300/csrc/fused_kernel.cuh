@@ -421,11 +421,12 @@ __global__ void __launch_bounds__(NT, 1)
     }
     __syncthreads();
 
-    // a sample's descriptor (uniform reads: kernel parameters for a single
-    // sample; the lanes' indexed reads in issue() use the shared copy)
+    // a sample's descriptor: kernel parameters, which lanes read at one
+    // index per tile or per pair (the copy issue reads the column bases at
+    // a per-lane index from the shared copy instead)
     auto SD = [&](int s) -> const SampleDesc& {
         if constexpr (FLAT)
-            return s_samples[s];
+            return B.s[s];
         else
             return B.s[0];
     };
