@@ -17,7 +17,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -46,6 +45,13 @@ def parse():
                    help="size factor of the 12-sample batched set (1.0: 0.2M to 20M events per sample)")
     p.add_argument("--dense-events", type=int, default=60_000_000,
                    help="events of the dense scale set (12 jets, 2.5 muons per event); 0 skips it")
+    # profiler-target mode: run one workload a few times, print its device time
+    p.add_argument("--profile", choices=["plain", "batched", "dense", "op"], default=None,
+                   help="run one workload --runs times (a target for ncu) instead of the benchmark")
+    p.add_argument("--op", default="sum_in_offsets", help="--profile op: the per-operation kernel")
+    p.add_argument("--kin", choices=["f32", "bf16", "f16"], default="f32", help="--profile: kinematic column type")
+    p.add_argument("--variations", type=int, default=1, help="--profile: jet-pt variations")
+    p.add_argument("--runs", type=int, default=3, help="--profile: runs after one untimed run")
     return p.parse_args()
 
 
@@ -76,27 +82,47 @@ def algorithmic_bytes(batch) -> int:
     return tot + batch.weight.nbytes
 
 
-def chain_traffic(kernel_src_sha):
-    """DRAM bytes per launch of the chain kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "chain_plain_10m.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != kernel_src_sha:
-        return None
-    return float(m.group(1))
-
-
 def kernel_source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1906_06242_gb300", "csrc")
-    for fn in ("chain.cu", "chain_kernel.cuh", "hepacc_tiles.cuh", "hepacc_device.cuh"):
+    for fn in ("chain.cu", "chain_kernel.cuh", "fused_kernel.cuh", "hepacc_tiles.cuh", "hepacc_device.cuh"):
         h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
+
+
+def profile_counters():
+    """Per-event counters of the fused chain kernel, one ncu capture per
+    form (profiles/counters.json; the captures and their commands are in the
+    summaries beside it): DRAM bytes read + written and warp instructions
+    per event. Valid only while the kernel sources hash to the recorded
+    value; {} otherwise."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "counters.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return {}
+    return d.get("forms", {})
+
+
+def issue_roofline(events, ms, form, clock_mhz):
+    """Roofline of an issue-bound form: warp instructions per second (the
+    events times the form's instructions per event from profile_counters)
+    against the SMs' issue peak, one warp instruction per scheduler per
+    cycle: SMs x 4 x the SM clock sampled under load. None without
+    counters for the form."""
+    import torch
+    c = profile_counters().get(form)
+    if not c or not ms or not clock_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * 4 * clock_mhz * 1e6
+    achieved = events * c["warp_instructions_per_event"] / (ms * 1e-3)
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_event": c["warp_instructions_per_event"],
+            "peak_from": f"{sms} SMs x 4 schedulers x {clock_mhz:.0f} MHz (sampled)",
+            "counters_from": c.get("capture")}
 
 
 class ClockSampler:
@@ -225,9 +251,98 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """One workload, one untimed run then ``--runs`` runs, for profiler
+    captures: ``plain`` (one sample of the benchmark generator, int64
+    offsets, ``--events``), ``dense`` (the dense scale set's generator:
+    Poisson 12 jets, 2.5 muons), ``batched`` (the 12-sample set scaled by
+    ``--batched-scale`` as one plan without autotuning or graph, every
+    launch a plain kernel launch), ``op`` (one per-operation kernel on the
+    jets of the plain sample). Prints the mean device time per run."""
+    import numpy as np
+    import torch
+    from paper_1906_06242_gb300 import hepacc as H
+    from paper_1906_06242_gb300 import synth
+    H.load()
+    shifts = synth.variation_shifts(args.variations)
+    cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [np.float32(1.0 + 0.01 * k) for k in shifts])
+    if args.profile in ("plain", "dense"):
+        if args.profile == "plain":
+            batch = synth.generate(args.events, 1)
+        else:
+            w = synth.WORKLOADS["scale_60m"]
+            batch = synth.generate(args.events, w["seed"], lam_jet=w["lam_jet"], lam_mu=w["lam_mu"],
+                                   lam_el=w["lam_el"], offset_dtype=w["offset_dtype"])
+        if args.kin != "f32":
+            batch = synth.reduced_precision(batch, args.kin)
+        db = H.DeviceBatch.from_host(batch)
+        out = H.ChainOutputs(cfg, batch.n_events)
+        st = (db.c_struct(), cfg.c_struct(), out.c_struct())
+
+        def run():
+            H.hepacc_run_chain(db, cfg, out, _structs=st)
+        n = batch.n_events
+    elif args.profile == "batched":
+        samples = synth.batched_samples(12, size_scale=args.batched_scale)
+        if args.kin != "f32":
+            samples = [synth.reduced_precision(s, args.kin) for s in samples]
+        dbs = [H.DeviceBatch.from_host(s) for s in samples]
+        outs = [H.ChainOutputs(cfg, s.n_events) for s in samples]
+        plan = H.hepacc_plan_create(cfg, dbs, outs, flags=H.PLAN_HIST_GLOBAL)
+        run = plan.run
+        n = sum(s.n_events for s in samples)
+    else:
+        batch = synth.generate(args.events, 1)
+        db = H.DeviceBatch.from_host(batch)
+        C, jo, mo = db.cols, db.offsets["jet"], db.offsets["mu"]
+        n = batch.n_events
+        f = torch.zeros(n, dtype=torch.float32, device="cuda")
+        i = torch.zeros(n, dtype=torch.int32, device="cuda")
+        i3 = torch.zeros((n, 3), dtype=torch.int32, device="cuda")
+        mj = torch.empty(C["jet_pt"].numel(), dtype=torch.uint8, device="cuda")
+        mm = torch.ones(C["mu_pt"].numel(), dtype=torch.uint8, device="cuda")
+        ej = torch.empty(C["jet_pt"].numel(), dtype=torch.float32, device="cuda")
+        edges = torch.from_numpy(H.hist_edges(20.0, 500.0, 100)).cuda()
+        hc = torch.zeros(102, dtype=torch.int64, device="cuda")
+        hw = torch.zeros(102, dtype=torch.float64, device="cuda")
+        edges_eta = torch.from_numpy(H.hist_edges(-2.5, 2.5, 30)).cuda()
+        hc2 = torch.zeros((102, 32), dtype=torch.int64, device="cuda")
+        hw2 = torch.zeros((102, 32), dtype=torch.float64, device="cuda")
+        ops = {
+            "sum_in_offsets": lambda: H.hepacc_sum_in_offsets(C["jet_pt"], jo, out=f),
+            "max_in_offsets": lambda: H.hepacc_max_in_offsets(C["jet_pt"], jo, out=f, arg=i),
+            "get_in_offsets": lambda: H.hepacc_get_in_offsets(C["jet_pt"], jo, 0, out=f, index=i),
+            "select_range": lambda: H.hepacc_select_range(C["jet_pt"], lo=30.0, mask_out=mj),
+            "scale": lambda: H.hepacc_scale(C["jet_pt"], 1.01, out=ej),
+            "mask_deltar": lambda: H.hepacc_mask_deltar(C["jet_eta"], C["jet_phi"], jo, C["mu_eta"], C["mu_phi"], mo,
+                                                        mask2=mm, mask1_out=mj),
+            "fill_histogram": lambda: H.hepacc_fill_histogram(C["jet_pt"], edges, counts=hc, sumw=hw, sumw2=None,
+                                                              with_sumw2=False),
+            "max_pt_trijet": lambda: H.hepacc_max_pt_trijet(C["jet_pt"], C["jet_eta"], C["jet_phi"], C["jet_mass"],
+                                                            jo, out_mass=f, out_idx3=i3),
+            "trijet_closest_mass": lambda: H.hepacc_trijet_closest_mass(C["jet_pt"], C["jet_eta"], C["jet_phi"],
+                                                                        C["jet_mass"], jo, out_mass=f, out_idx3=i3),
+            "fill_histogram_nd": lambda: H.hepacc_fill_histogram_nd([C["jet_pt"], C["jet_eta"]], [edges, edges_eta],
+                                                                    counts=hc2, sumw=hw2, with_sumw2=False),
+        }
+        run = ops[args.op]
+    run()   # first run: module load and launch set-up
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.runs):
+        run()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / max(1, args.runs)
+    print(json.dumps({"profile": args.profile, "events": int(n), "ms_per_run": ms, "device_error": H.device_error()}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -371,17 +486,24 @@ def main():
     if not args.no_extra and rank == 0:
         # the streamed dense form first: its host-to-device copies ran at a
         # third of the link's rate when measured after the other forms
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
         if args.dense_events > 0:
-            extra.update(dense_forms(H, synth, torch, stream, args.dense_events))
+            extra.update(dense_forms(H, synth, torch, stream, args.dense_events, mhz))
         extra.update(secondary_forms(H, synth, batch, torch, stream))
         extra["kernels"] = kernel_forms(H, batch, torch, stream)
-        extra.update(batched_forms(H, synth, torch, stream, args.batched_scale))
+        extra.update(batched_forms(H, synth, torch, stream, args.batched_scale, mhz))
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(batch, 4_000_000) if world == 1 else None
+    # DRAM traffic of one launch: bytes per event of the committed capture
+    # (a smaller case of the same kernel, traffic proportional to the events)
+    counters = profile_counters()
+    traffic = None
+    if "plain_f32" in counters:
+        traffic = counters["plain_f32"]["dram_bytes_per_event"] * batch.n_events
     if world == 1 and not args.no_extra:
         extra["cpu_oracle_all_cores"] = cpu_oracle_all_cores(batch, 4_000_000)
     line = {
@@ -394,10 +516,12 @@ def main():
                    "parallelism": f"dp{world} (independent event shards)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
-                     "traffic": chain_traffic(kernel_source_sha()), "kernel": "k_chain",
+                     "traffic": traffic, "traffic_from": counters.get("plain_f32", {}).get("capture"),
+                     "kernel": "k_fused",
                      "algorithmic_bytes_per_launch": int(alg_bytes),
                      "avg_kernel_ms": avg_kernel_ms,
                      "median_kernel_ms": sorted(kern_ms)[len(kern_ms) // 2], "min_kernel_ms": min(kern_ms)},
+        "issue_roofline": issue_roofline(batch.n_events, avg_kernel_ms, "plain_f32", clocks.get("sm_mhz")),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps,
@@ -542,7 +666,7 @@ def kernel_forms(H, batch, torch, stream):
     return res
 
 
-def batched_forms(H, synth, torch, stream, scale):
+def batched_forms(H, synth, torch, stream, scale, mhz=None):
     """The batching form: 12 samples of uneven size (log-uniform 0.2M to 20M
     events, seeds 11 to 22), each with 21 jet-pt variations, BF16 kinematic
     columns and FP16 btag, in one autotuned persistent launch replayed as a
@@ -582,6 +706,7 @@ def batched_forms(H, synth, torch, stream, scale):
     ms = timeit(per_sample, k=5)
     nbytes = sum(d.nbytes_read() for d in dbs)
     res["plain_calls_12x21"] = {"events_per_s": n_tot / (ms * 1e-3), "ms_per_step": ms,
+                                "roofline": issue_roofline(n_tot, ms, "calls_f32_21", mhz),
                                 "event_variations_per_s": N_VARIATIONS_BATCHED * n_tot / (ms * 1e-3),
                                 "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9, "launches": len(samples),
                                 "form": "FP32 columns, one fused hepacc_run_chain call per sample"}
@@ -609,6 +734,7 @@ def batched_forms(H, synth, torch, stream, scale):
     ms = timeit(plan.run, k=10)
     nbytes = sum(d.nbytes_read() for d in dbs)
     res["batched_bf16_12x21"] = {"events_per_s": n_tot / (ms * 1e-3), "ms_per_step": ms,
+                                 "roofline": issue_roofline(n_tot, ms, "batched_bf16_21", mhz),
                                  "event_variations_per_s": N_VARIATIONS_BATCHED * n_tot / (ms * 1e-3),
                                  "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9, "algorithmic_bytes": int(nbytes),
                                  "events": int(n_tot), "samples": [int(s.n_events) for s in hs],
@@ -620,7 +746,7 @@ def batched_forms(H, synth, torch, stream, scale):
     return res
 
 
-def dense_forms(H, synth, torch, stream, n_events):
+def dense_forms(H, synth, torch, stream, n_events, mhz=None):
     """The scale form: dense events (Poisson 12 jets, 2.5 muons, 0.8
     electrons; drawn in 5M-event chunks from seed 5) resident in HBM as FP32
     and as BF16 columns, and the FP32 set streamed from pinned host memory
@@ -660,7 +786,8 @@ def dense_forms(H, synth, torch, stream, n_events):
         H.hepacc_run_chain(db, cfg, out, stream=stream, _structs=st)
         res[name] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms,
                      "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9, "algorithmic_bytes": int(nbytes),
-                     "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "events": int(batch.n_events)}
+                     "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "events": int(batch.n_events),
+                     "roofline": issue_roofline(batch.n_events, ms, name.replace("_resident", ""), mhz)}
         return out
 
     ref = resident(b, "dense_resident_f32")
