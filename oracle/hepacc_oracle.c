@@ -637,6 +637,33 @@ void oracle_select_opposite_sign(const int8_t *charge, const void *off, int ot, 
  * get_bin_contents (Section III kernel list): histogram lookup
  * ------------------------------------------------------------------------- */
 
+/* Linear interpolation of the contents (nbins+2 entries, with under- and
+ * overflow) between the centres c_b = (edges[b-1] + edges[b]) / 2 of
+ * neighbouring in-range bins, at a non-NaN v: contents[1] below c_1,
+ * contents[nbins] at or above c_nbins, else with c_b <= v < c_b+1
+ * contents[b] + (v - c_b) / (c_b+1 - c_b) * (contents[b+1] - contents[b]),
+ * each operation in binary32 rounded as written. */
+static float lookup_interp(float v, const float *edges, int nbins, const float *contents)
+{
+    float c1 = (edges[0] + edges[1]) * 0.5f;
+    float cn = (edges[nbins - 1] + edges[nbins]) * 0.5f;
+    if (nbins == 1 || v < c1)
+        return contents[1];
+    if (v >= cn)
+        return contents[nbins];
+    for (int b = 1; b < nbins; b++) {
+        float cb = (edges[b - 1] + edges[b]) * 0.5f;
+        float cb1 = (edges[b] + edges[b + 1]) * 0.5f;
+        if (v >= cb && v < cb1) {
+            float tt = (v - cb) / (cb1 - cb);
+            float d = contents[b + 1] - contents[b];
+            float prod = tt * d;
+            return contents[b] + prod;
+        }
+    }
+    return contents[nbins];
+}
+
 /* out[j] = contents[b] with b the bin of x[j] (bin_of; contents has nbins+2
  * entries, under- and overflow included); NaN for NaN input. With
  * interpolate set: linear interpolation between the contents of
@@ -657,27 +684,7 @@ void oracle_get_bin_contents(const void *x, int xt, int64_t m, const float *edge
             out[j] = contents[bin_of((double)v, edges, nbins)];
             continue;
         }
-        float c1 = (edges[0] + edges[1]) * 0.5f;
-        float cn = (edges[nbins - 1] + edges[nbins]) * 0.5f;
-        if (nbins == 1 || v < c1) {
-            out[j] = contents[1];
-            continue;
-        }
-        if (v >= cn) {
-            out[j] = contents[nbins];
-            continue;
-        }
-        for (int b = 1; b < nbins; b++) {
-            float cb = (edges[b - 1] + edges[b]) * 0.5f;
-            float cb1 = (edges[b] + edges[b + 1]) * 0.5f;
-            if (v >= cb && v < cb1) {
-                float tt = (v - cb) / (cb1 - cb);
-                float d = contents[b + 1] - contents[b];
-                float prod = tt * d;
-                out[j] = contents[b] + prod;
-                break;
-            }
-        }
+        out[j] = lookup_interp(v, edges, nbins, contents);
     }
 }
 
@@ -711,7 +718,26 @@ typedef struct {
     int n_hist;              /* must be 20 */
     const int32_t *nbins;    /* [n_hist] */
     const float *edges;      /* concatenated, nbins[h] + 1 per histogram */
+    /* jet-energy corrections (NULL jec_contents: the scales): per variation
+     * a table of (jec_neta + 2) rows, one per eta bin with under- and
+     * overflow, of jec_npt + 2 contents over the pt bins */
+    int jec_neta, jec_npt;
+    const float *jec_eta_edges, *jec_pt_edges;
+    const float *jec_contents;   /* [n_var][jec_neta + 2][jec_npt + 2] */
 } oracle_config;
+
+/* The jet-energy correction of variation k for a jet (pt, eta) (Section IV:
+ * corrections looked up in binned tables, linearly interpolated): the row of
+ * the jet's eta bin (bin_of, under- and overflow rows included) read at the
+ * jet's pt by lookup_interp; NaN for a NaN pt or eta. */
+static float jec_factor(const oracle_config *c, int k, float pt, float eta)
+{
+    int row = bin_of((double)eta, c->jec_eta_edges, c->jec_neta);
+    if (row < 0 || isnan(pt))
+        return NAN;
+    const float *r = c->jec_contents + ((int64_t)k * (c->jec_neta + 2) + row) * (c->jec_npt + 2);
+    return lookup_interp(pt, c->jec_pt_edges, c->jec_npt, r);
+}
 
 typedef struct {
     uint64_t *counts;        /* [n_var][total bins] */
@@ -806,8 +832,10 @@ void oracle_run_chain(const oracle_batch *b, const oracle_config *c, oracle_outp
             float lead_pt = 0.0f, sub_pt = 0.0f, max_bt = 0.0f;
             int have_bt = 0;
             for (int64_t i = j0; i < j1; i++) {
-                float ptk = get_f(b->jet_pt, kt, i) * s;
                 float eta = get_f(b->jet_eta, kt, i), phi = get_f(b->jet_phi, kt, i);
+                float pt = get_f(b->jet_pt, kt, i);
+                /* the variation's jet pt: scaled, or corrected by its table */
+                float ptk = c->jec_contents ? pt * jec_factor(c, k, pt, eta) : pt * s;
                 int sel = ptk > c->jet_pt_min && fabsf(eta) < c->jet_abseta_max;
                 for (int flav = 0; flav < 2 && sel; flav++) {
                     const void *off = flav == 0 ? b->mu_off : b->el_off;

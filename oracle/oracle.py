@@ -310,7 +310,9 @@ class _Config(ctypes.Structure):
                 ("lep_iso_max", ctypes.c_float), ("jet_pt_min", ctypes.c_float),
                 ("jet_abseta_max", ctypes.c_float), ("dr2_cut", ctypes.c_float),
                 ("btag_min", ctypes.c_float), ("n_var", ctypes.c_int), ("scales", ctypes.c_void_p),
-                ("n_hist", ctypes.c_int), ("nbins", ctypes.c_void_p), ("edges", ctypes.c_void_p)]
+                ("n_hist", ctypes.c_int), ("nbins", ctypes.c_void_p), ("edges", ctypes.c_void_p),
+                ("jec_neta", ctypes.c_int), ("jec_npt", ctypes.c_int), ("jec_eta_edges", ctypes.c_void_p),
+                ("jec_pt_edges", ctypes.c_void_p), ("jec_contents", ctypes.c_void_p)]
 
 
 class _Outputs(ctypes.Structure):
@@ -360,13 +362,16 @@ def get_bin_contents(x, edges, contents, interpolate=False, fmt=None):
     return out
 
 
-def run_chain(batch, cuts, hist_specs, shifts, per_event=True, kin_fmt=None, btag_fmt=None):
+def run_chain(batch, cuts, hist_specs, shifts, per_event=True, kin_fmt=None, btag_fmt=None, jec=None):
     """Run the benchmark chain on a seeded batch (the object made by the input
     generator, read through its attributes only). ``shifts`` are the integer k
     of the jet-pt scales 1 + 0.01 k. Returns a dict of numpy arrays:
     counts/sumw/sumw2 [n_var, total_bins]; with ``per_event`` also pass,
     nlep, njet, nb, idx [n_var, 5, N], vars [n_var, 20, N] (float64),
-    gap [n_var, N] and idx2 [n_var, 3, N]."""
+    gap [n_var, N] and idx2 [n_var, 3, N]. ``jec`` (optional): jet-energy
+    correction tables, dict of eta_edges, pt_edges and contents
+    [n_var][n_eta + 2][n_pt + 2] (float32); the variations then correct each
+    jet's pt by its table instead of scaling it."""
     n = int(batch.n_events)
     c = batch.cols
     kin_fmt = kin_fmt or getattr(batch, "kin_fmt", None)
@@ -411,6 +416,15 @@ def run_chain(batch, cuts, hist_specs, shifts, per_event=True, kin_fmt=None, bta
     cfg.n_hist = len(hist_specs)
     cfg.nbins = P(nbins)
     cfg.edges = P(edges)
+    if jec is not None:
+        # jet-energy corrections: eta_edges, pt_edges (float32) and contents
+        # [n_var][len(eta_edges) + 1][len(pt_edges) + 1] (float32)
+        ee = np.ascontiguousarray(jec["eta_edges"], dtype=np.float32)
+        pe = np.ascontiguousarray(jec["pt_edges"], dtype=np.float32)
+        ct = np.ascontiguousarray(jec["contents"], dtype=np.float32)
+        assert ct.shape == (nv, len(ee) + 1, len(pe) + 1), ct.shape
+        cfg.jec_neta, cfg.jec_npt = len(ee) - 1, len(pe) - 1
+        cfg.jec_eta_edges, cfg.jec_pt_edges, cfg.jec_contents = P(ee), P(pe), P(ct)
     total_bins = int((nbins + 2).sum())
 
     out = {"counts": np.zeros((nv, total_bins), dtype=np.uint64),

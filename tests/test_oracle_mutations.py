@@ -29,7 +29,7 @@ MUTATIONS = [
     ("get counts from 1", "if (seen == want) {\n                found = i;", "if (seen == want + 1) {\n                found = i;"),
     ("sub-leading may be leading", "if (q == lead_q)\n                    continue;", ""),
     ("chain dR inclusive", "< c->dr2_cut)\n                            sel = 0;", "<= c->dr2_cut)\n                            sel = 0;"),
-    ("jet pt unscaled", "float ptk = get_f(b->jet_pt, kt, i) * s;", "float ptk = get_f(b->jet_pt, kt, i);"),
+    ("jet pt unscaled", "pt * jec_factor(c, k, pt, eta) : pt * s;", "pt * jec_factor(c, k, pt, eta) : pt;"),
     ("HT in FP64", "ht += ptk;", "ht = (float)((double)ht + (double)ptk + 1e-7 * ptk);"),
     ("weight squared missing", "o->sumw2[at] += w * w;", "o->sumw2[at] += w;"),
     ("set writes next", "((uint8_t *)x)[i] = (uint8_t)value;", "((uint8_t *)x)[i + 1] = (uint8_t)value;"),
@@ -37,7 +37,7 @@ MUTATIONS = [
     ("closest mass uses max", "double d = fabs(m - target);", "double d = -fabs(m - target);"),
     ("opposite sign is different", "(int)charge[i] * (int)charge[j] < 0", "charge[i] != charge[j]"),
     ("opposite sign ignores mask", "if (on(mask_in, j) && ", "if ("),
-    ("lookup interpolates from the upper bin", "out[j] = contents[b] + prod;", "out[j] = contents[b + 1] - prod;"),
+    ("lookup interpolates from the upper bin", "return contents[b] + prod;", "return contents[b + 1] - prod;"),
     ("lookup centre is the lower edge", "float cb = (edges[b - 1] + edges[b]) * 0.5f;", "float cb = edges[b - 1];"),
     ("nd stride drops the flow bins", "cell = cell * (nbins[d] + 2) + b;", "cell = cell * (nbins[d] + 1) + b;"),
     ("nd NaN goes to underflow", "skip = 1;\n                break;", "b = 0;"),
@@ -51,6 +51,10 @@ MUTATIONS = [
     ("pair index at the count allowed", "a >= i1 - i0 || b >= i1 - i0", "a > i1 - i0 || b > i1 - i0"),
     ("pair index not rebased", "a += i0;\n        b += i0;", "a += 0;\n        b += 0;"),
     ("pair negative index allowed", "if (a < 0 || b < 0 ||", "if ("),
+    ("jec row of the eta bin below", "int row = bin_of((double)eta, c->jec_eta_edges, c->jec_neta);",
+     "int row = bin_of((double)eta, c->jec_eta_edges, c->jec_neta);\n    row = row > 0 ? row - 1 : row;"),
+    ("jec looks up the row at the lower edge", "return lookup_interp(pt, c->jec_pt_edges, c->jec_npt, r);",
+     "return r[bin_of((double)pt, c->jec_pt_edges, c->jec_npt)];"),
 ]
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

@@ -914,3 +914,59 @@ def test_pair_mass_local_indices_and_sliced_offsets(orc):
     # rows with mask_rows unset keep their value (NaN here)
     masked = orc.pair_mass(pt, eta, phi, m, off, ia, ib, mask_rows=np.array([0, 1, 1, 1, 1], dtype=np.uint8))
     assert np.isnan(masked[0]) and masked[1] == got[1]
+
+
+# ---------------------------------------------------------------------------
+# jet-energy corrections by table lookup (Section IV), linear in pt
+# ---------------------------------------------------------------------------
+
+def test_jec_constant_tables_equal_the_scales(orc):
+    # a table whose every entry is float32(1 + 0.01 k) corrects every jet by
+    # exactly that factor, so variation k is the scale variation k
+    b = synth.generate(20_011, 12)
+    shifts = [0, 3, -3]
+    eta_e = np.array([-2.5, -1.0, 0.0, 1.0, 2.5], dtype=F32)
+    pt_e = np.array([20, 30, 50, 80, 150, 400], dtype=F32)
+    contents = np.stack([np.full((len(eta_e) + 1, len(pt_e) + 1), F32(1.0 + 0.01 * k), dtype=F32) for k in shifts])
+    jec = dict(eta_edges=eta_e, pt_edges=pt_e, contents=contents)
+    a = orc.run_chain(b, synth.CUTS, synth.HIST_SPECS, shifts, jec=jec)
+    s = orc.run_chain(b, synth.CUTS, synth.HIST_SPECS, shifts)
+    for key in ("pass", "njet", "nb", "idx", "counts", "sumw"):
+        np.testing.assert_array_equal(a[key], s[key], err_msg=key)
+    np.testing.assert_array_equal(np.isnan(a["vars"]), np.isnan(s["vars"]))
+    ok = ~np.isnan(s["vars"])
+    np.testing.assert_array_equal(a["vars"][ok], s["vars"][ok])
+
+
+def test_jec_hand_event(orc):
+    # eta rows: [-2.5, 0) -> row 1, [0, 2.5) -> row 2; pt bin centres 30, 50,
+    # 70, 100. Variation 0: row 1 = 1.5, 1.25, 1.0, 0.75; row 2 = 2.0, 1.5,
+    # 1.0, 0.5 (flow entries 9, never read). Jets, far from the muon in phi:
+    #   pt 50  at eta -1.0: centre 50, factor 1.25 -> 62.5
+    #   pt 100 at eta  1.0: centre 100, factor 0.5 -> 50
+    #   pt 60  at eta -0.5: halfway 50..70, 1.25 + 0.5 (1.0 - 1.25) = 1.125 -> 67.5
+    #   pt 25  at eta  0.5: below the first centre, factor 2.0 -> 50
+    #   pt 200 at eta -2.0: above the last centre, factor 0.75 -> 150
+    # all exact in binary32: 5 jets, HT = 380, leading 150, b-jet the first.
+    # Variation 1: every entry 0.5 -> 25, 50, 30, 12.5, 100: two jets above
+    # 30 (30 itself fails), the b-jet (25) not selected: no pass, HT = 150.
+    ev = {"jet": [{"pt": 50, "eta": -1.0, "phi": 2.0, "mass": 5, "btag": 0.9},
+                   {"pt": 100, "eta": 1.0, "phi": 2.5, "mass": 5, "btag": 0.1},
+                   {"pt": 60, "eta": -0.5, "phi": 3.0, "mass": 5, "btag": 0.1},
+                   {"pt": 25, "eta": 0.5, "phi": -2.0, "mass": 5, "btag": 0.1},
+                   {"pt": 200, "eta": -2.0, "phi": -2.5, "mass": 5, "btag": 0.1}],
+          "mu": [{"pt": 50, "eta": 0.0, "phi": 0.0, "mass": 0.1, "iso": 0.01, "tight": 1, "charge": 1}],
+          "el": [], "weight": 1.0}
+    b = synth.hand_batch([ev])
+    eta_e = np.array([-2.5, 0.0, 2.5], dtype=F32)
+    pt_e = np.array([20, 40, 60, 80, 120], dtype=F32)
+    c = np.full((2, 4, 6), 9.0, dtype=F32)
+    c[0, 1, 1:5] = [1.5, 1.25, 1.0, 0.75]
+    c[0, 2, 1:5] = [2.0, 1.5, 1.0, 0.5]
+    c[1, :, :] = 0.5
+    o = orc.run_chain(b, synth.CUTS, synth.HIST_SPECS, [0, 1], jec=dict(eta_edges=eta_e, pt_edges=pt_e, contents=c))
+    assert o["njet"][0, 0] == 5 and o["nb"][0, 0] == 1 and o["pass"][0, 0] == 1
+    assert o["vars"][0, VAR["ht"], 0] == 380.0 and o["vars"][0, VAR["lead_jet_pt"], 0] == 150.0
+    assert o["vars"][0, VAR["sublead_jet_pt"], 0] == 67.5
+    assert o["njet"][1, 0] == 2 and o["nb"][1, 0] == 0 and o["pass"][1, 0] == 0
+    assert o["vars"][1, VAR["ht"], 0] == 150.0
