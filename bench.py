@@ -567,6 +567,21 @@ def secondary_forms(H, synth, batch, torch, stream):
     ref_pass = ref.ev_pass.clone()
     ref_counts = ref.counts.clone()
     del ref, db
+    # 21 variations as jet-pt scales and as (eta, pt) correction tables
+    # (Section IV: corrections looked up in binned tables, interpolated)
+    shifts21 = synth.variation_shifts(N_VARIATIONS_BATCHED)
+    db = H.DeviceBatch.from_host(batch)
+    for name, jec in (("fused_scales_21", None), ("fused_jec_tables_21", synth.jec_tables(shifts21))):
+        c21 = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [np.float32(1.0 + 0.01 * k) for k in shifts21], jec=jec)
+        o21 = H.ChainOutputs(c21, batch.n_events)
+        s21 = (db.c_struct(), c21.c_struct(), o21.c_struct())
+        ms = timeit(lambda: H.hepacc_run_chain(db, c21, o21, stream=stream, _structs=s21), k=10, w=2)
+        res[name] = {"events_per_s": batch.n_events / (ms * 1e-3), "ms_per_step": ms,
+                     "event_variations_per_s": N_VARIATIONS_BATCHED * batch.n_events / (ms * 1e-3),
+                     "variations": N_VARIATIONS_BATCHED,
+                     "form": "FP32 columns, one call" + (", per-jet table lookups" if jec else ", scales")}
+        del o21
+    del db
     for fmt in ("bf16", "f16"):
         hb = synth.reduced_precision(batch, fmt)
         dh = H.DeviceBatch.from_host(hb)

@@ -291,6 +291,7 @@ hepacc_status hepacc_get_bin_contents(const void *data, hepacc_dtype data_type, 
  * ------------------------------------------------------------------------- */
 
 #define HEPACC_CHAIN_NVARS 20
+#define HEPACC_JEC_MAX_BINS 64
 #define HEPACC_MAX_VARIATIONS 64
 #define HEPACC_CHAIN_MAX_EDGES 4096
 
@@ -334,6 +335,20 @@ typedef struct {
     const float *scales;                   /* [n_var] jet-pt scale factors, finite and > 0 */
     int32_t nbins[HEPACC_CHAIN_NVARS];
     const float *edges;                    /* sum (nbins[h]+1) <= HEPACC_CHAIN_MAX_EDGES */
+    /* Jet-energy corrections by table lookup (Section IV), optional: with
+     * jec_contents non-NULL the variations correct each jet's pt instead of
+     * scaling it: variation k takes the row of the jet's eta bin
+     * (jec_eta_edges, jec_neta bins, rows for under- and overflow
+     * included) of its table and reads it at the jet's pt as
+     * hepacc_get_bin_contents interpolates (jec_pt_edges, jec_npt bins):
+     * pt_k = pt * factor (binary32); scales are then ignored (but must still
+     * be valid). Edges HOST (copied), increasing, 1 <= bins <=
+     * HEPACC_JEC_MAX_BINS; contents DEVICE float32
+     * [n_var][jec_neta + 2][jec_npt + 2], read by the kernels (valid while
+     * calls and plans that use them run). */
+    int32_t jec_neta, jec_npt;
+    const float *jec_eta_edges, *jec_pt_edges;
+    const float *jec_contents;
 } hepacc_chain_config;
 
 /* Outputs, DEVICE memory. counts, sumw (and sumw2 if non-NULL) are

@@ -56,6 +56,26 @@ hepacc_status make_params(const hepacc_chain_config* cfg, ChainParams& P) {
     }
     P.n_edges = ne;
     P.total_bins = nbt;
+    if (cfg->jec_contents) {
+        const int na = cfg->jec_neta, np = cfg->jec_npt;
+        if (na < 1 || na > HEPACC_JEC_MAX_BINS || np < 1 || np > HEPACC_JEC_MAX_BINS)
+            return fail(HEPACC_ERR_INVALID_ARG, "correction tables need 1 to %d bins per axis", HEPACC_JEC_MAX_BINS);
+        if (!cfg->jec_eta_edges || !cfg->jec_pt_edges) return fail(HEPACC_ERR_INVALID_ARG, "correction table edges are required");
+        for (int i = 0; i <= na; ++i) {
+            if (i > 0 && !(cfg->jec_eta_edges[i] > cfg->jec_eta_edges[i - 1]))
+                return fail(HEPACC_ERR_INVALID_ARG, "correction eta edges are not increasing");
+            P.jec_edges[i] = cfg->jec_eta_edges[i];
+        }
+        for (int i = 0; i <= np; ++i) {
+            if (i > 0 && !(cfg->jec_pt_edges[i] > cfg->jec_pt_edges[i - 1]))
+                return fail(HEPACC_ERR_INVALID_ARG, "correction pt edges are not increasing");
+            P.jec_edges[na + 1 + i] = cfg->jec_pt_edges[i];
+        }
+        P.jec_neta = na;
+        P.jec_npt = np;
+        P.jec_contents = cfg->jec_contents;
+        P.jec_eta_invw = static_cast<float>(na) / (cfg->jec_eta_edges[na] - cfg->jec_eta_edges[0]);
+    }
     return HEPACC_OK;
 }
 
@@ -249,6 +269,7 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
     L.bars = region(at, 8 * fused::kMaxStages + 6 * 8);
     L.edges = region(at, static_cast<size_t>(P.n_edges) * 4);
     L.scales = region(at, static_cast<size_t>(P.n_var) * 4);
+    L.jec = region(at, static_cast<size_t>(P.jec_contents ? P.jec_neta + P.jec_npt + 2 : 1) * 4);
     L.samples = region(at, static_cast<size_t>(std::max(flat_samples, 1)) * sizeof(SampleDesc));
     L.misc = region(at, fused::kMiscWords * 4 + sizeof(L.col));   // counter, warp totals, column specs
     const DeviceInfo di = device_info();
@@ -685,8 +706,10 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     const int modes[3][3] = {{H_SMEM, 1, HEPACC_PLAN_HIST_BLOCK},
                              {H_CLUSTER, 8, HEPACC_PLAN_HIST_CLUSTER8},
                              {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16}};
+    // (the walking kernel applies scales only: plans with correction
+    // tables run the compacting kernel)
     for (const auto& m : modes) {
-        for (int e = kMaxThreadsBatched; e >= 64 && (allowed & m[2]); e -= 32) {
+        for (int e = kMaxThreadsBatched; e >= 64 && (allowed & m[2]) && !p->P.jec_contents; e -= 32) {
             Candidate c{};
             if (layout_for(e, m[0], m[1], lam_j, lam_m, lam_e, kes, bes, kMinBlocksBatched, p->P, c.L)) {
                 c.compacting = false;

@@ -74,6 +74,11 @@ struct ChainParams {
     int boff[kNV];      // first bin of histogram h inside a variation block
     float invw[kNV];    // bins per unit of histogram h (first guess of the bin search)
     float e_lo[kNV], e_hi[kNV];   // first and last edge of histogram h
+    // jet-energy correction tables (jec_contents null: the scales)
+    int jec_neta, jec_npt;
+    const float* jec_contents;    // DEVICE [n_var][jec_neta + 2][jec_npt + 2]
+    float jec_eta_invw;
+    float jec_edges[2 * (HEPACC_JEC_MAX_BINS + 1)];   // eta edges, then pt edges
     float edges[HEPACC_CHAIN_MAX_EDGES];
 };
 

@@ -58,6 +58,7 @@ struct FLayout {
     uint32_t bars;          // full[S] mbarriers
     uint32_t edges;         // histogram edges (n_edges floats)
     uint32_t scales;        // n_var floats
+    uint32_t jec;           // jet-energy correction edges: eta, then pt
     uint32_t samples;       // flat launches: the samples' descriptors
     int cap_ev, cap_j;      // buffer capacity: events, jets
     // buffered events
@@ -175,21 +176,72 @@ struct ColJets {
     __device__ __forceinline__ void cs(int i, float& c, float& s) const { sincosf(phi(i), &s, &c); }
 };
 
-// One (event, variation): the jets selected under scale s (accepted and
-// fl(pt s) > cut), their counts, HT and mass sum in element order, the
+// Jet-energy correction tables in shared memory (edges) and global memory
+// (contents, [n_var][neta + 2][npt + 2]).
+struct JecTab {
+    const float* eta_e;   // neta + 1 edges
+    const float* pt_e;    // npt + 1 edges
+    const float* contents;
+    int neta, npt;
+    float eta_invw;       // eta bins per unit (first guess of the bin search)
+};
+
+// The correction of variation k for a jet (pt, eta): the row of the jet's eta
+// bin (under- and overflow rows included) read at the jet's pt by linear
+// interpolation between the centres c_b = (e[b-1] + e[b]) / 2 of the pt
+// bins, clamped to the first and last centre, each operation in binary32
+// rounded as written (the lookup of hepacc_get_bin_contents). NaN for a NaN
+// pt or eta.
+__device__ __forceinline__ float jec_factor(const JecTab& t, int k, float pt, float eta) {
+    const int row = find_bin(eta, t.eta_e, t.neta, t.eta_invw);
+    if (row < 0 || pt != pt) return qnan();
+    const float* r = t.contents + (static_cast<int64_t>(k) * (t.neta + 2) + row) * (t.npt + 2);
+    const int nb = t.npt;
+    auto centre = [&](int b) { return __fmul_rn(__fadd_rn(t.pt_e[b - 1], t.pt_e[b]), 0.5f); };
+    if (nb == 1 || pt < centre(1)) return __ldg(r + 1);
+    if (pt >= centre(nb)) return __ldg(r + nb);
+    int lo = 1, hi = nb - 1;   // the smallest b with pt < c_{b+1} (then c_b <= pt)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pt < centre(mid + 1))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const float cb = centre(lo), cb1 = centre(lo + 1);
+    const float yb = __ldg(r + lo), yb1 = __ldg(r + lo + 1);
+    const float u = __fdiv_rn(__fsub_rn(pt, cb), __fsub_rn(cb1, cb));
+    return __fadd_rn(yb, __fmul_rn(u, __fsub_rn(yb1, yb)));
+}
+
+// A variation's jet pt: pt scaled by s, or corrected by the variation's
+// table (jec).
+struct VarPt {
+    float s;
+    int k;
+    bool jec;
+    JecTab t;
+    __device__ __forceinline__ float operator()(float pt, float eta) const {
+        return __fmul_rn(pt, jec ? jec_factor(t, k, pt, eta) : s);
+    }
+};
+
+// One (event, variation): the jets selected under the variation (accepted
+// and pt_k > cut, pt_k = ptk_of(pt, eta)), their counts, HT and mass sum in element order, the
 // leading and sub-leading jet (first occurrence on ties), the max btag,
 // the triplet with the largest |sum pT| (first in lexicographic order on
 // ties; ranked in binary32 from sin/cos of phi), the dijet and trijet
 // masses. Fills v[0..12], v[18] and the counts and indices.
 template <class JS>
-__device__ __forceinline__ void process_pair(const JS& J, float s, const ChainParams& P, PairRes& R) {
+__device__ __forceinline__ void process_pair(const JS& J, const VarPt& ptk_of, const ChainParams& P, PairRes& R) {
+    auto ptk_at = [&](int i) { return ptk_of(J.pt(i), J.eta(i)); };
     const int n = J.n;
     float ht = 0.0f, summ = 0.0f, maxbt = qnan(), lead_pt = 0.0f, sub_pt = 0.0f;
     int lead = -1, sub = -1, nsel = 0, nbj = 0;
     uint64_t selm = 0;   // selected jets among the first 64
     for (int i = 0; i < n; ++i) {
         if (!J.acc(i)) continue;
-        const float ptk = __fmul_rn(J.pt(i), s);
+        const float ptk = ptk_at(i);
         if (!(ptk > P.jet_pt_min)) continue;
         const float bt = J.btag(i);
         nbj += bt > P.btag_min ? 1 : 0;
@@ -229,19 +281,19 @@ __device__ __forceinline__ void process_pair(const JS& J, float s, const ChainPa
                 const int a = __ffsll(static_cast<long long>(ma)) - 1;
                 float ca, sa;
                 J.cs(a, ca, sa);
-                const float pa = __fmul_rn(J.pt(a), s);
+                const float pa = ptk_at(a);
                 const float ax = pa * ca, ay = pa * sa;
                 for (uint64_t mb = ma & (ma - 1); mb; mb &= mb - 1) {
                     const int b = __ffsll(static_cast<long long>(mb)) - 1;
                     float cb, sb;
                     J.cs(b, cb, sb);
-                    const float pb = __fmul_rn(J.pt(b), s);
+                    const float pb = ptk_at(b);
                     const float bx = ax + pb * cb, by = ay + pb * sb;
                     for (uint64_t mc = mb & (mb - 1); mc; mc &= mc - 1) {
                         const int c = __ffsll(static_cast<long long>(mc)) - 1;
                         float cc, sc;
                         J.cs(c, cc, sc);
-                        const float pc = __fmul_rn(J.pt(c), s);
+                        const float pc = ptk_at(c);
                         const float tx = bx + pc * cc, ty = by + pc * sc;
                         const float val = tx * tx + ty * ty;
                         if (val > best) {
@@ -254,24 +306,24 @@ __device__ __forceinline__ void process_pair(const JS& J, float s, const ChainPa
                 }
             }
         } else {
-            auto sel = [&](int i) { return J.acc(i) && __fmul_rn(J.pt(i), s) > P.jet_pt_min; };
+            auto sel = [&](int i) { return J.acc(i) && ptk_at(i) > P.jet_pt_min; };
             for (int a = 0; a < n; ++a) {
                 if (!sel(a)) continue;
                 float ca, sa;
                 J.cs(a, ca, sa);
-                const float pa = __fmul_rn(J.pt(a), s);
+                const float pa = ptk_at(a);
                 const float ax = pa * ca, ay = pa * sa;
                 for (int b = a + 1; b < n; ++b) {
                     if (!sel(b)) continue;
                     float cb, sb;
                     J.cs(b, cb, sb);
-                    const float pb = __fmul_rn(J.pt(b), s);
+                    const float pb = ptk_at(b);
                     const float bx = ax + pb * cb, by = ay + pb * sb;
                     for (int c = b + 1; c < n; ++c) {
                         if (!sel(c)) continue;
                         float cc, sc;
                         J.cs(c, cc, sc);
-                        const float pc = __fmul_rn(J.pt(c), s);
+                        const float pc = ptk_at(c);
                         const float tx = bx + pc * cc, ty = by + pc * sc;
                         const float val = tx * tx + ty * ty;
                         if (val > best) {
@@ -305,7 +357,7 @@ __device__ __forceinline__ void process_pair(const JS& J, float s, const ChainPa
         auto obj = [&](int i) {
             if (i == lead) return ol;
             if (i == sub) return os;
-            return mass_obj(__fmul_rn(J.pt(i), s), J.eta(i), J.phi(i), J.mass(i));
+            return mass_obj(ptk_at(i), J.eta(i), J.phi(i), J.mass(i));
         };
         const MassObj oa = obj(ta), ob = obj(tb), oc = obj(tc);
         auto pd = [&](int i, const MassObj& x, int j, const MassObj& y) {
@@ -404,6 +456,11 @@ __global__ void __launch_bounds__(NT, 1)
 
     for (int i = tid; i < P.n_edges; i += NT) s_edges[i] = P.edges[i];
     for (int i = tid; i < P.n_var; i += NT) s_scales[i] = P.scales[i];
+    float* s_jec = reinterpret_cast<float*>(smem + L.jec);
+    const bool use_jec = P.jec_contents != nullptr;
+    if (use_jec)
+        for (int i = tid; i < P.jec_neta + P.jec_npt + 2; i += NT) s_jec[i] = P.jec_edges[i];
+    const JecTab jt{s_jec, s_jec + P.jec_neta + 1, P.jec_contents, P.jec_neta, P.jec_npt, P.jec_eta_invw};
     // the samples' descriptors and the column specifications in shared
     // memory: lanes read them at different indices, which the constant bank
     // holding kernel parameters would serialise
@@ -573,7 +630,7 @@ __global__ void __launch_bounds__(NT, 1)
             const int j0 = b_j0[ev];
             BufJets J{j_pt + j0, j_eta + j0, j_phi + j0, j_m + j0, j_bt + j0, j_c + j0, j_s + j0, j_acc + j0, b_nj[ev]};
             PairRes R;
-            process_pair(J, s_scales[k], P, R);
+            process_pair(J, VarPt{s_scales[k], k, use_jec, jt}, P, R);
             if (b_nlep[ev] >= 1) {
                 R.v[13] = b_lpt[ev];
                 R.v[14] = b_leta[ev];
@@ -717,7 +774,7 @@ __global__ void __launch_bounds__(NT, 1)
             const bool active = valid && (DEBUG || nlep == 1);
             // thresholds: second-largest accepted jet pt, largest accepted b-tagged pt
             float p1 = -INFINITY, p2 = -INFINITY, pb = -INFINITY;
-            if (active && nlep == 1) {
+            if (active && nlep == 1 && !use_jec) {
                 for (int i = rs[0]; i < rt[0]; ++i) {
                     if (!jet_acc<KT>(T, P, i, 1, leta, lphi, 0, 0, 0, 0)) continue;
                     const float pt = Elem<KT>::f(T.template ld<KT>(J_PT, i));
@@ -731,10 +788,34 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
             uint64_t pm = 0;
-            if (active && nlep == 1) {
+            if (active && nlep == 1 && !use_jec) {
                 for (int k = 0; k < P.n_var; ++k) {
                     const float s = s_scales[k];
                     if (__fmul_rn(p2, s) > P.jet_pt_min && __fmul_rn(pb, s) > P.jet_pt_min) pm |= 1ull << k;
+                }
+            }
+            if (active && nlep == 1 && use_jec) {
+                // corrected jets need no common order: every variation
+                // counts its selected jets and b-jets (accepted jets as a
+                // mask; past 64 jets acceptance is evaluated again)
+                const int nj = rt[0] - rs[0];
+                uint64_t am = 0;
+                if (nj <= 64)
+                    for (int i = 0; i < nj; ++i)
+                        if (jet_acc<KT>(T, P, rs[0] + i, 1, leta, lphi, 0, 0, 0, 0)) am |= 1ull << i;
+                for (int k = 0; k < P.n_var; ++k) {
+                    const VarPt vp{s_scales[k], k, true, jt};
+                    int ns = 0, nbs = 0;
+                    for (int i = 0; i < nj; ++i) {
+                        if (nj <= 64 ? ((am >> i) & 1ull) == 0 : !jet_acc<KT>(T, P, rs[0] + i, 1, leta, lphi, 0, 0, 0, 0))
+                            continue;
+                        const float ptk = vp(Elem<KT>::f(T.template ld<KT>(J_PT, rs[0] + i)),
+                                             Elem<KT>::f(T.template ld<KT>(J_ETA, rs[0] + i)));
+                        if (!(ptk > P.jet_pt_min)) continue;
+                        ++ns;
+                        nbs += Elem<BT>::f(T.template ld<BT>(J_BTAG, rs[0] + i)) > P.btag_min ? 1 : 0;
+                    }
+                    if (ns >= 2 && nbs >= 1) pm |= 1ull << k;
                 }
             }
             const uint64_t qm = DEBUG ? (valid ? (P.n_var >= 64 ? ~0ull : ((1ull << P.n_var) - 1ull)) : 0ull) : pm;
@@ -820,7 +901,7 @@ __global__ void __launch_bounds__(NT, 1)
                 for (uint64_t m = qm; m; m &= m - 1) {
                     const int k = __ffsll(static_cast<long long>(m)) - 1;
                     PairRes R;
-                    process_pair(J, s_scales[k], P, R);
+                    process_pair(J, VarPt{s_scales[k], k, use_jec, jt}, P, R);
                     if (nlep >= 1) {
                         R.v[13] = lpt;
                         R.v[14] = leta;

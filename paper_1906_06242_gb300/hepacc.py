@@ -363,7 +363,8 @@ class ChainConfigC(ctypes.Structure):
                 ("lep_iso_max", ctypes.c_float), ("jet_pt_min", ctypes.c_float),
                 ("jet_abseta_max", ctypes.c_float), ("dr2_cut", ctypes.c_float), ("btag_min", ctypes.c_float),
                 ("n_var", ctypes.c_int32), ("scales", _c_void_p), ("nbins", ctypes.c_int32 * NVARS),
-                ("edges", _c_void_p)]
+                ("edges", _c_void_p), ("jec_neta", ctypes.c_int32), ("jec_npt", ctypes.c_int32),
+                ("jec_eta_edges", _c_void_p), ("jec_pt_edges", _c_void_p), ("jec_contents", _c_void_p)]
 
 
 class ChainOutputsC(ctypes.Structure):
@@ -460,9 +461,12 @@ def hist_edges(lo, hi, nbins):
 
 
 class ChainConfig:
-    """Cuts, jet-pt scales and histogram edges of the chain (host memory)."""
+    """Cuts, jet-pt scales and histogram edges of the chain (host memory);
+    optionally jet-energy correction tables (``jec``: dict of eta_edges,
+    pt_edges (host, float32) and contents, a float32 tensor
+    [n_var][n_eta + 2][n_pt + 2], moved to the device)."""
 
-    def __init__(self, cuts, hist_specs, scales):
+    def __init__(self, cuts, hist_specs, scales, jec=None):
         if len(hist_specs) != NVARS:
             raise ValueError(f"the chain fills exactly {NVARS} histograms")
         self.cuts = dict(cuts)
@@ -472,6 +476,14 @@ class ChainConfig:
         self.edges = np.concatenate([hist_edges(h[1], h[2], h[3]) for h in hist_specs]).astype(np.float32)
         self.total_bins = int((self.nbins + 2).sum())
         self.bin_offsets = np.concatenate([[0], np.cumsum(self.nbins + 2)[:-1]]).astype(np.int64)
+        self.jec = None
+        if jec is not None:
+            ee = np.ascontiguousarray(jec["eta_edges"], dtype=np.float32)
+            pe = np.ascontiguousarray(jec["pt_edges"], dtype=np.float32)
+            ct = torch.as_tensor(np.asarray(jec["contents"], dtype=np.float32)).contiguous().cuda()
+            if tuple(ct.shape) != (len(self.scales), len(ee) + 1, len(pe) + 1):
+                raise ValueError(f"correction contents must be [n_var][n_eta + 2][n_pt + 2], got {tuple(ct.shape)}")
+            self.jec = (ee, pe, ct)
 
     @property
     def n_var(self):
@@ -487,6 +499,10 @@ class ChainConfig:
         for h in range(NVARS):
             c.nbins[h] = int(self.nbins[h])
         c.edges = self.edges.ctypes.data
+        if self.jec is not None:
+            ee, pe, ct = self.jec
+            c.jec_neta, c.jec_npt = len(ee) - 1, len(pe) - 1
+            c.jec_eta_edges, c.jec_pt_edges, c.jec_contents = ee.ctypes.data, pe.ctypes.data, ct.data_ptr()
         return c
 
 

@@ -340,3 +340,21 @@ def hand_batch(events, offset_dtype=np.int64) -> EventBatch:
     w = np.array([ev.get("weight", 1.0) for ev in events], dtype=np.float32)
     return EventBatch(n_events=len(events), jet_offsets=offsets["jet"], mu_offsets=offsets["mu"],
                       el_offsets=offsets["el"], cols=cols, weight=w)
+
+
+def jec_tables(shifts, seed: int = 101, n_eta: int = 8, n_pt: int = 24):
+    """Synthetic jet-energy correction tables (inputs standing in for the
+    experiment's correction files, which are not available): eta edges
+    uniform over [-2.5, 2.5], pt edges log-uniform over [20, 1000] GeV, and
+    for variation k (shift k) contents 1 + 0.01 k plus a smooth random
+    (eta, pt) dependence of a few per cent, float32, shape [n_var][n_eta +
+    2][n_pt + 2] (rows and columns for under- and overflow included)."""
+    rng = np.random.default_rng(seed)
+    eta_edges = np.linspace(-2.5, 2.5, n_eta + 1).astype(np.float32)
+    pt_edges = np.geomspace(20.0, 1000.0, n_pt + 1).astype(np.float32)
+    a = rng.uniform(-0.03, 0.03, size=(n_eta + 2, 1))
+    b = rng.uniform(-0.02, 0.02, size=(1, n_pt + 2))
+    shape = np.sin(np.linspace(0.0, 3.0, n_pt + 2))[None, :]
+    base = 1.0 + a + b * shape
+    contents = np.stack([(base + 0.01 * k).astype(np.float32) for k in shifts])
+    return {"eta_edges": eta_edges, "pt_edges": pt_edges, "contents": contents}

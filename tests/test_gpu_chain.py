@@ -22,9 +22,9 @@ def H():
     return hepacc
 
 
-def run_gpu(H, batch, shifts, per_event=True, sumw2=True):
+def run_gpu(H, batch, shifts, per_event=True, sumw2=True, jec=None):
     cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, synth.variation_scales(1) if shifts is None else
-                        [np.float32(1.0 + 0.01 * k) for k in shifts])
+                        [np.float32(1.0 + 0.01 * k) for k in shifts], jec=jec)
     db = H.DeviceBatch.from_host(batch)
     out = H.ChainOutputs(cfg, batch.n_events, per_event=per_event, sumw2=sumw2)
     H.hepacc_run_chain(db, cfg, out)
@@ -38,9 +38,9 @@ def run_gpu(H, batch, shifts, per_event=True, sumw2=True):
     return res
 
 
-def check(H, orc, batch, shifts, per_event=True):
-    o = orc.run_chain(batch, synth.CUTS, synth.HIST_SPECS, shifts)
-    g = run_gpu(H, batch, shifts, per_event=per_event)
+def check(H, orc, batch, shifts, per_event=True, jec=None):
+    o = orc.run_chain(batch, synth.CUTS, synth.HIST_SPECS, shifts, jec=jec)
+    g = run_gpu(H, batch, shifts, per_event=per_event, jec=jec)
     stats = {}
     if per_event:
         stats.update(CC.compare_per_event(g, o, shifts))
@@ -174,3 +174,29 @@ def test_chain_too_dense_for_any_stage(H, orc):
     # and histograms, against the oracle)
     batch = synth.generate(1_501, 91, lam_jet=60.0, lam_mu=6.0)
     check(H, orc, batch, [0, 5])
+
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+def test_chain_jet_energy_corrections(H, orc, fmt):
+    # variations that correct each jet's pt by an (eta, pt) table
+    # (Section IV), per event and per histogram against the oracle
+    batch = synth.generate(40_013, 17, offset_dtype=np.int32)
+    if fmt != "f32":
+        batch = synth.reduced_precision(batch, fmt)
+    shifts = synth.variation_shifts(5)
+    print(fmt, check(H, orc, batch, shifts, jec=synth.jec_tables(shifts)))
+
+
+def test_chain_constant_corrections_equal_scales(H):
+    # a table whose every entry is float32(1 + 0.01 k) is the scale variation k
+    batch = synth.generate(30_007, 19)
+    shifts = [0, 2, -2]
+    t = synth.jec_tables(shifts)
+    t["contents"] = np.stack([np.full_like(t["contents"][0], np.float32(1.0 + 0.01 * k)) for k in shifts])
+    a = run_gpu(H, batch, shifts, jec=t)
+    b = run_gpu(H, batch, shifts)
+    for key in ("pass", "njet", "nb", "idx", "counts"):
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+    np.testing.assert_array_equal(a["vars"], b["vars"])
+    assert H.device_error() == 0

@@ -171,3 +171,24 @@ def test_plan_reused_over_batches(H, orc, flags):
     for st, os_ in zip(sets, outs):
         res = [(o.counts.cpu().numpy().view(np.uint64), o.sumw.cpu().numpy(), o.sumw2.cpu().numpy()) for o in os_]
         check_samples(orc, st, shifts, res)
+
+
+
+def test_plan_with_jet_energy_corrections(H, orc):
+    # a plan whose variations correct jets by table lookup (compacting kernel)
+    samples = [synth.generate(n, 500 + i, offset_dtype=np.int64) for i, n in enumerate([15_013, 4_001, 9_007])]
+    shifts = synth.variation_shifts(7)
+    jec = synth.jec_tables(shifts)
+    cfg = H.ChainConfig(synth.CUTS, synth.HIST_SPECS, [np.float32(1.0 + 0.01 * k) for k in shifts], jec=jec)
+    dbs = [H.DeviceBatch.from_host(s) for s in samples]
+    outs = [H.ChainOutputs(cfg, s.n_events) for s in samples]
+    plan = H.hepacc_plan_create(cfg, dbs, outs, flags=1 | 2)
+    plan.run()
+    torch.cuda.synchronize()
+    assert plan.describe()["chosen"]["kernel"] == "compacting"
+    plan.close()
+    assert H.device_error() == 0
+    for s, o in zip(samples, outs):
+        ref = orc.run_chain(s, synth.CUTS, synth.HIST_SPECS, shifts, jec=jec)
+        CC.compare_hists(o.counts.cpu().numpy().view(np.uint64), o.sumw.cpu().numpy(), o.sumw2.cpu().numpy(), ref,
+                         s.weight, ref["nbins"], ref["edges"])
