@@ -83,10 +83,16 @@ def algorithmic_bytes(batch) -> int:
 
 
 def kernel_source_sha():
+    """Hash of the chain kernel's code (comments and blank space removed, so
+    that a comment edit leaves recorded counters valid)."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1906_06242_gb300", "csrc")
     for fn in ("chain.cu", "chain_kernel.cuh", "fused_kernel.cuh", "hepacc_tiles.cuh", "hepacc_device.cuh"):
-        h.update(open(os.path.join(csrc, fn), "rb").read())
+        src = open(os.path.join(csrc, fn), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
@@ -395,6 +401,8 @@ def main():
             step()
         torch.cuda.synchronize()
     clocks = clock.stop()
+    if H.device_error():
+        raise RuntimeError("the chain kernel set the device error word during the timed steps")
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in ev]
     if dist:
@@ -481,6 +489,8 @@ def main():
                "form": "streaming.StreamedChain: %d host ranges, copies overlapping the chain" % len(sc.ranges),
                "serial": serial}
         del sc, out3
+        if H.device_error():
+            raise RuntimeError("the chain kernel set the device error word in the end-to-end forms")
 
     extra = {}
     if not args.no_extra and rank == 0:
@@ -493,6 +503,8 @@ def main():
         extra["kernels"] = kernel_forms(H, batch, torch, stream)
         extra.update(batched_forms(H, synth, torch, stream, args.batched_scale, mhz))
 
+    if H.device_error():
+        raise RuntimeError("a kernel set the device error word in the secondary forms")
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -345,7 +345,9 @@ typedef struct {
      * be valid). Edges HOST (copied), increasing, 1 <= bins <=
      * HEPACC_JEC_MAX_BINS; contents DEVICE float32
      * [n_var][jec_neta + 2][jec_npt + 2], read by the kernels (valid while
-     * calls and plans that use them run). */
+     * calls and plans that use them run). With tables the batch's btag
+     * column is F32 for F32 kinematics and F16 for half kinematics
+     * (HEPACC_ERR_DTYPE otherwise). */
     int32_t jec_neta, jec_npt;
     const float *jec_eta_edges, *jec_pt_edges;
     const float *jec_contents;

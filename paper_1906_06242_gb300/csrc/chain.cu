@@ -275,10 +275,13 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
     const DeviceInfo di = device_info();
     const size_t limit =
         std::min(static_cast<size_t>(di.smem_per_sm / blocks_per_sm - di.smem_reserved), static_cast<size_t>(di.smem_optin));
-    const size_t slack = 16 * 24;   // alignment of the buffer's regions
+    const bool jec = P.jec_contents != nullptr;
+    const size_t slack = 16 * (jec ? 26 : 24);   // alignment of the buffer's regions
     if (at + slack >= limit) return false;
     const size_t avail = limit - at - slack;
-    const size_t per_ev = 11 * 4 + 2 * 8, per_j = 7 * 4 + 1;
+    // per buffered jet: 7 floats and the acceptance byte, with correction
+    // tables also its table position (int32 offset, float weight)
+    const size_t per_ev = 11 * 4 + 2 * 8, per_j = 7 * 4 + 1 + (jec ? 8 : 0);
     int cap_ev = std::min(2 * NT, 65535);
     if (static_cast<size_t>(cap_ev) * per_ev + 4 * 32 * per_j > avail) cap_ev = NT;
     if (static_cast<size_t>(cap_ev) * per_ev + 4 * 32 * per_j > avail) return false;
@@ -307,6 +310,10 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
     L.j_c = region(at, nj * 4);
     L.j_s = region(at, nj * 4);
     L.j_acc = region(at, nj);
+    if (jec) {
+        L.j_jo = region(at, nj * 4);
+        L.j_ju = region(at, nj * 4);
+    }
     L.total = static_cast<uint32_t>((at + 15) & ~size_t(15));
     return L.total <= limit;
 }
@@ -388,6 +395,7 @@ extern "C" hepacc_status hepacc_run_chain(const hepacc_event_batch* b, const hep
     a.btag_type = b->btag_type;
     a.debug = has_per_event(out);
     a.flat = false;
+    a.jec = P.jec_contents != nullptr;
     a.block = NT;
     a.grid = 0;
     a.cap_grid = true;
@@ -462,6 +470,7 @@ hepacc_status launch_one(const hepacc_plan* p, const Candidate& c, const BatchDe
         a.btag_type = p->btag;
         a.debug = false;
         a.flat = true;
+        a.jec = p->P.jec_contents != nullptr;
         a.block = c.block;
         a.grid = 0;
         a.cap_grid = false;
@@ -683,46 +692,47 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     // objects per event so dense that nothing fits: smaller stages (tiles
     // that do not fit one are read from global memory)
     for (double f = 1.0; cands.empty() && f >= 1.0 / 64; f *= 0.5) {
-    const double lam_j = lam_j0 * f, lam_m = lam_m0 * f, lam_e = lam_e0 * f;
-    if (allowed & HEPACC_PLAN_HIST_GLOBAL) {
-        // block size x blocks per SM (the share of the SM's shared memory
-        // each block is laid out for) x stages
-        for (int nt : fused::kBlocks)
-            for (int bps = 1; bps * nt <= 256; ++bps)
-                for (int S = 2; S <= fused::kMaxStages; ++S) {
-                    Candidate c{};
-                    if (fused_layout(nt, S, lam_j, lam_m, lam_e, kes, bes, p->P, flat_samples, bps, c.FL) &&
-                        c.FL.cap_j >= nt * lam_j) {
-                        c.compacting = true;
-                        c.hmode = H_GLOBAL;
-                        c.cluster = 1;
-                        c.block = nt;
-                        c.blocks_per_sm = bps;
-                        c.stages = S;
-                        cands.push_back(c);
+        const double lam_j = lam_j0 * f, lam_m = lam_m0 * f, lam_e = lam_e0 * f;
+        if (allowed & HEPACC_PLAN_HIST_GLOBAL) {
+            // block size x blocks per SM (the share of the SM's shared memory
+            // each block is laid out for) x stages
+            // (correction tables: blocks of kDebugBlock threads only)
+            for (int nt : fused::kBlocks)
+                for (int bps = 1; bps * nt <= 256 && (!p->P.jec_contents || nt == fused::kDebugBlock); ++bps)
+                    for (int S = 2; S <= fused::kMaxStages; ++S) {
+                        Candidate c{};
+                        if (fused_layout(nt, S, lam_j, lam_m, lam_e, kes, bes, p->P, flat_samples, bps, c.FL) &&
+                            c.FL.cap_j >= nt * lam_j) {
+                            c.compacting = true;
+                            c.hmode = H_GLOBAL;
+                            c.cluster = 1;
+                            c.block = nt;
+                            c.blocks_per_sm = bps;
+                            c.stages = S;
+                            cands.push_back(c);
+                        }
                     }
+        }
+        const int modes[3][3] = {{H_SMEM, 1, HEPACC_PLAN_HIST_BLOCK},
+                                 {H_CLUSTER, 8, HEPACC_PLAN_HIST_CLUSTER8},
+                                 {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16}};
+        // (the walking kernel applies scales only: plans with correction
+        // tables run the compacting kernel)
+        for (const auto& m : modes) {
+            for (int e = kMaxThreadsBatched; e >= 64 && (allowed & m[2]) && !p->P.jec_contents; e -= 32) {
+                Candidate c{};
+                if (layout_for(e, m[0], m[1], lam_j, lam_m, lam_e, kes, bes, kMinBlocksBatched, p->P, c.L)) {
+                    c.compacting = false;
+                    c.hmode = m[0];
+                    c.cluster = m[1];
+                    c.block = e;
+                    c.blocks_per_sm = kMinBlocksBatched;
+                    c.stages = 2;
+                    cands.push_back(c);
+                    break;
                 }
-    }
-    const int modes[3][3] = {{H_SMEM, 1, HEPACC_PLAN_HIST_BLOCK},
-                             {H_CLUSTER, 8, HEPACC_PLAN_HIST_CLUSTER8},
-                             {H_CLUSTER, 16, HEPACC_PLAN_HIST_CLUSTER16}};
-    // (the walking kernel applies scales only: plans with correction
-    // tables run the compacting kernel)
-    for (const auto& m : modes) {
-        for (int e = kMaxThreadsBatched; e >= 64 && (allowed & m[2]) && !p->P.jec_contents; e -= 32) {
-            Candidate c{};
-            if (layout_for(e, m[0], m[1], lam_j, lam_m, lam_e, kes, bes, kMinBlocksBatched, p->P, c.L)) {
-                c.compacting = false;
-                c.hmode = m[0];
-                c.cluster = m[1];
-                c.block = e;
-                c.blocks_per_sm = kMinBlocksBatched;
-                c.stages = 2;
-                cands.push_back(c);
-                break;
             }
         }
-    }
     }
     if (cands.empty()) return drop(fail(HEPACC_ERR_INVALID_ARG, "no chain layout fits in shared memory"));
     p->n_candidates = static_cast<int>(cands.size());

@@ -15,7 +15,10 @@
 //    Delta R) and keeps two thresholds, the second-largest accepted jet pt
 //    p2 and the largest accepted b-tagged jet pt pb, which decide every
 //    jet-pt variation s_k: fl(p2 s_k) > cut and fl(pb s_k) > cut (x ->
-//    fl(x s) is non-decreasing for s > 0).
+//    fl(x s) is non-decreasing for s > 0). With jet-energy correction
+//    tables (a factor per jet and variation) there is no common order: each
+//    accepted jet's table position is found once and every variation counts
+//    its selected jets and b-jets directly (as bit masks over variations).
 //  * compaction: an event that passes any variation appends its summary and
 //    all its jets (lanes over the warp's queued jets) to a block-wide buffer
 //    in shared memory; a warp reserves its space with one atomic.
@@ -24,7 +27,9 @@
 //    and the mass sum in element order, the leading pair, the max-|sum pT|
 //    triplet, the invariant masses, the 20 variables and their histogram
 //    fills (global atomics). With per-event outputs every event is queued
-//    and writes its outputs here.
+//    and writes its outputs here. The drain first computes, once per
+//    buffered accepted jet, sin and cos of phi and (with tables) the jet's
+//    table position, which every variation of the event then reuses.
 // A warp whose reservation does not fit processes its events' pairs itself
 // (thread = event) from the stage; so does a tile that is not staged.
 #pragma once
@@ -67,6 +72,7 @@ struct FLayout {
     // buffered jets
     uint32_t j_pt, j_eta, j_phi, j_m, j_bt, j_c, j_s;   // float
     uint32_t j_acc;         // uint8
+    uint32_t j_jo, j_ju;    // int32, float: correction-table positions (tables only)
     uint32_t misc;          // counter word (events << 16 | jets), warp scan scratch, column specifications
     uint32_t total;
 };
@@ -138,11 +144,66 @@ __device__ __forceinline__ bool jet_acc(const A& T, const ChainParams& P, int i,
     return true;
 }
 
+// Jet-energy correction tables in shared memory (edges) and global memory
+// (contents, [n_var][neta + 2][npt + 2]).
+struct JecTab {
+    const float* eta_e;   // neta + 1 edges
+    const float* pt_e;    // npt + 1 edges
+    const float* contents;
+    int neta, npt;
+    float eta_invw;       // eta bins per unit (first guess of the bin search)
+};
+
+// Where a jet (pt, eta) reads every variation's table: the offset, inside
+// one variation's [neta + 2][npt + 2] table, of the pt bin b of its eta row
+// (under- and overflow rows included) and the interpolation weight u, such
+// that the correction of variation k is y_b + u (y_{b+1} - y_b) with y the
+// row of table k. Between the centres c_b = (e[b-1] + e[b]) / 2 of the pt
+// bins u = (pt - c_b) / (c_{b+1} - c_b); below the first centre b = 1 and
+// above the last b = npt, both with u = 0 (clamped, so y_b exactly); every
+// operation binary32 rounded as written (the lookup of
+// hepacc_get_bin_contents). A NaN pt or eta gives u = NaN (a NaN factor).
+struct JecPos {
+    int off;
+    float u;
+};
+__device__ __forceinline__ JecPos jec_pos(const JecTab& t, float pt, float eta) {
+    const int row = find_bin(eta, t.eta_e, t.neta, t.eta_invw);
+    if (row < 0 || pt != pt) return JecPos{0, qnan()};
+    const int rb = row * (t.npt + 2);
+    const int nb = t.npt;
+    auto centre = [&](int b) { return __fmul_rn(__fadd_rn(t.pt_e[b - 1], t.pt_e[b]), 0.5f); };
+    if (nb == 1 || pt < centre(1)) return JecPos{rb + 1, 0.0f};
+    if (pt >= centre(nb)) return JecPos{rb + nb, 0.0f};
+    int lo = 1, hi = nb - 1;   // the smallest b with pt < c_{b+1} (then c_b <= pt)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pt < centre(mid + 1))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const float cb = centre(lo), cb1 = centre(lo + 1);
+    return JecPos{rb + lo, __fdiv_rn(__fsub_rn(pt, cb), __fsub_rn(cb1, cb))};
+}
+
+// The correction of variation k at a jet's position (y_b + 0 = y_b at the
+// clamped ends: the tables hold finite values).
+__device__ __forceinline__ float jec_factor(const JecTab& t, int k, JecPos q) {
+    const float* r = t.contents + static_cast<int64_t>(k) * ((t.neta + 2) * (t.npt + 2)) + q.off;
+    const float yb = __ldg(r), yb1 = __ldg(r + 1);
+    return __fadd_rn(yb, __fmul_rn(q.u, __fsub_rn(yb1, yb)));
+}
+
 // Jets of one event in the shared-memory buffer (binary32, widened).
 struct BufJets {
     const float *pt_, *eta_, *phi_, *m_, *bt_, *c_, *s_;
     const uint8_t* acc_;
+    const int* jo_;     // correction-table positions of the accepted jets (with tables)
+    const float* ju_;
     int n;
+    template <class TB>
+    __device__ __forceinline__ JecPos jpos(int i, const TB&) const { return JecPos{jo_[i], ju_[i]}; }
     __device__ __forceinline__ bool acc(int i) const { return acc_[i] != 0; }
     __device__ __forceinline__ float pt(int i) const { return pt_[i]; }
     __device__ __forceinline__ float eta(int i) const { return eta_[i]; }
@@ -174,55 +235,23 @@ struct ColJets {
     __device__ __forceinline__ float mass(int i) const { return Elem<KT>::f(T.template ld<KT>(J_MASS, j0 + i)); }
     __device__ __forceinline__ float btag(int i) const { return Elem<BT>::f(T.template ld<BT>(J_BTAG, j0 + i)); }
     __device__ __forceinline__ void cs(int i, float& c, float& s) const { sincosf(phi(i), &s, &c); }
+    template <class TB>
+    __device__ __forceinline__ JecPos jpos(int i, const TB& t) const { return jec_pos(t, pt(i), eta(i)); }
 };
 
-// Jet-energy correction tables in shared memory (edges) and global memory
-// (contents, [n_var][neta + 2][npt + 2]).
-struct JecTab {
-    const float* eta_e;   // neta + 1 edges
-    const float* pt_e;    // npt + 1 edges
-    const float* contents;
-    int neta, npt;
-    float eta_invw;       // eta bins per unit (first guess of the bin search)
-};
-
-// The correction of variation k for a jet (pt, eta): the row of the jet's eta
-// bin (under- and overflow rows included) read at the jet's pt by linear
-// interpolation between the centres c_b = (e[b-1] + e[b]) / 2 of the pt
-// bins, clamped to the first and last centre, each operation in binary32
-// rounded as written (the lookup of hepacc_get_bin_contents). NaN for a NaN
-// pt or eta.
-__device__ __forceinline__ float jec_factor(const JecTab& t, int k, float pt, float eta) {
-    const int row = find_bin(eta, t.eta_e, t.neta, t.eta_invw);
-    if (row < 0 || pt != pt) return qnan();
-    const float* r = t.contents + (static_cast<int64_t>(k) * (t.neta + 2) + row) * (t.npt + 2);
-    const int nb = t.npt;
-    auto centre = [&](int b) { return __fmul_rn(__fadd_rn(t.pt_e[b - 1], t.pt_e[b]), 0.5f); };
-    if (nb == 1 || pt < centre(1)) return __ldg(r + 1);
-    if (pt >= centre(nb)) return __ldg(r + nb);
-    int lo = 1, hi = nb - 1;   // the smallest b with pt < c_{b+1} (then c_b <= pt)
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (pt < centre(mid + 1))
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    const float cb = centre(lo), cb1 = centre(lo + 1);
-    const float yb = __ldg(r + lo), yb1 = __ldg(r + lo + 1);
-    const float u = __fdiv_rn(__fsub_rn(pt, cb), __fsub_rn(cb1, cb));
-    return __fadd_rn(yb, __fmul_rn(u, __fsub_rn(yb1, yb)));
-}
-
-// A variation's jet pt: pt scaled by s, or corrected by the variation's
-// table (jec).
+// A variation's jet pt: pt scaled by s, or (JEC) corrected by the
+// variation's table at the jet's position (JS::jpos).
+template <bool JEC>
 struct VarPt {
     float s;
     int k;
-    bool jec;
     JecTab t;
-    __device__ __forceinline__ float operator()(float pt, float eta) const {
-        return __fmul_rn(pt, jec ? jec_factor(t, k, pt, eta) : s);
+    template <class JS>
+    __device__ __forceinline__ float operator()(const JS& J, int i) const {
+        if constexpr (JEC)
+            return __fmul_rn(J.pt(i), jec_factor(t, k, J.jpos(i, t)));
+        else
+            return __fmul_rn(J.pt(i), s);
     }
 };
 
@@ -232,9 +261,9 @@ struct VarPt {
 // the triplet with the largest |sum pT| (first in lexicographic order on
 // ties; ranked in binary32 from sin/cos of phi), the dijet and trijet
 // masses. Fills v[0..12], v[18] and the counts and indices.
-template <class JS>
-__device__ __forceinline__ void process_pair(const JS& J, const VarPt& ptk_of, const ChainParams& P, PairRes& R) {
-    auto ptk_at = [&](int i) { return ptk_of(J.pt(i), J.eta(i)); };
+template <class JS, class VP>
+__device__ __forceinline__ void process_pair(const JS& J, const VP& ptk_of, const ChainParams& P, PairRes& R) {
+    auto ptk_at = [&](int i) { return ptk_of(J, i); };
     const int n = J.n;
     float ht = 0.0f, summ = 0.0f, maxbt = qnan(), lead_pt = 0.0f, sub_pt = 0.0f;
     int lead = -1, sub = -1, nsel = 0, nbj = 0;
@@ -411,7 +440,7 @@ __device__ __forceinline__ void emit(const ChainParams& P, const float* s_edges,
     }
 }
 
-template <typename KT, typename BT, typename OffT, bool DEBUG, bool FLAT, int NT>
+template <typename KT, typename BT, typename OffT, bool DEBUG, bool FLAT, int NT, bool JEC>
 __global__ void __launch_bounds__(NT, 1)
     k_fused(const __grid_constant__ FLayout L, const __grid_constant__ ChainParams P,
             const __grid_constant__ BatchDesc B) {
@@ -453,12 +482,13 @@ __global__ void __launch_bounds__(NT, 1)
     float* j_c = reinterpret_cast<float*>(smem + L.j_c);
     float* j_s = reinterpret_cast<float*>(smem + L.j_s);
     uint8_t* j_acc = reinterpret_cast<uint8_t*>(smem + L.j_acc);
+    int32_t* j_jo = reinterpret_cast<int32_t*>(smem + L.j_jo);
+    float* j_ju = reinterpret_cast<float*>(smem + L.j_ju);
 
     for (int i = tid; i < P.n_edges; i += NT) s_edges[i] = P.edges[i];
     for (int i = tid; i < P.n_var; i += NT) s_scales[i] = P.scales[i];
     float* s_jec = reinterpret_cast<float*>(smem + L.jec);
-    const bool use_jec = P.jec_contents != nullptr;
-    if (use_jec)
+    if constexpr (JEC)
         for (int i = tid; i < P.jec_neta + P.jec_npt + 2; i += NT) s_jec[i] = P.jec_edges[i];
     const JecTab jt{s_jec, s_jec + P.jec_neta + 1, P.jec_contents, P.jec_neta, P.jec_npt, P.jec_eta_invw};
     // the samples' descriptors and the column specifications in shared
@@ -587,8 +617,16 @@ __global__ void __launch_bounds__(NT, 1)
         const int nev = static_cast<int>(cnt >> 16);
         const int nj = static_cast<int>(cnt & 0xffffu);
         // sin and cos of the accepted jets' phi, once for every variation
+        // (and their correction-table positions)
         for (int j = tid; j < nj; j += NT)
-            if (j_acc[j]) sincosf(j_phi[j], &j_s[j], &j_c[j]);
+            if (j_acc[j]) {
+                sincosf(j_phi[j], &j_s[j], &j_c[j]);
+                if constexpr (JEC) {
+                    const JecPos jp = jec_pos(jt, j_pt[j], j_eta[j]);
+                    j_jo[j] = jp.off;
+                    j_ju[j] = jp.u;
+                }
+            }
         // first pair of every event: block-wide exclusive scan of its variation count
         const int ept = (nev + NT - 1) / NT;
         const int lo = min(tid * ept, nev), hi = min(lo + ept, nev);
@@ -628,9 +666,10 @@ __global__ void __launch_bounds__(NT, 1)
             const int ev = a;
             const int k = nth_bit64(b_q[ev], i - b_ps[ev]);
             const int j0 = b_j0[ev];
-            BufJets J{j_pt + j0, j_eta + j0, j_phi + j0, j_m + j0, j_bt + j0, j_c + j0, j_s + j0, j_acc + j0, b_nj[ev]};
+            BufJets J{j_pt + j0, j_eta + j0, j_phi + j0, j_m + j0, j_bt + j0, j_c + j0, j_s + j0, j_acc + j0,
+                      j_jo + j0, j_ju + j0, b_nj[ev]};
             PairRes R;
-            process_pair(J, VarPt{s_scales[k], k, use_jec, jt}, P, R);
+            process_pair(J, VarPt<JEC>{s_scales[k], k, jt}, P, R);
             if (b_nlep[ev] >= 1) {
                 R.v[13] = b_lpt[ev];
                 R.v[14] = b_leta[ev];
@@ -774,7 +813,7 @@ __global__ void __launch_bounds__(NT, 1)
             const bool active = valid && (DEBUG || nlep == 1);
             // thresholds: second-largest accepted jet pt, largest accepted b-tagged pt
             float p1 = -INFINITY, p2 = -INFINITY, pb = -INFINITY;
-            if (active && nlep == 1 && !use_jec) {
+            if (!JEC && active && nlep == 1) {
                 for (int i = rs[0]; i < rt[0]; ++i) {
                     if (!jet_acc<KT>(T, P, i, 1, leta, lphi, 0, 0, 0, 0)) continue;
                     const float pt = Elem<KT>::f(T.template ld<KT>(J_PT, i));
@@ -788,35 +827,30 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
             uint64_t pm = 0;
-            if (active && nlep == 1 && !use_jec) {
+            if (!JEC && active && nlep == 1) {
                 for (int k = 0; k < P.n_var; ++k) {
                     const float s = s_scales[k];
                     if (__fmul_rn(p2, s) > P.jet_pt_min && __fmul_rn(pb, s) > P.jet_pt_min) pm |= 1ull << k;
                 }
             }
-            if (active && nlep == 1 && use_jec) {
-                // corrected jets need no common order: every variation
-                // counts its selected jets and b-jets (accepted jets as a
-                // mask; past 64 jets acceptance is evaluated again)
-                const int nj = rt[0] - rs[0];
-                uint64_t am = 0;
-                if (nj <= 64)
-                    for (int i = 0; i < nj; ++i)
-                        if (jet_acc<KT>(T, P, rs[0] + i, 1, leta, lphi, 0, 0, 0, 0)) am |= 1ull << i;
-                for (int k = 0; k < P.n_var; ++k) {
-                    const VarPt vp{s_scales[k], k, true, jt};
-                    int ns = 0, nbs = 0;
-                    for (int i = 0; i < nj; ++i) {
-                        if (nj <= 64 ? ((am >> i) & 1ull) == 0 : !jet_acc<KT>(T, P, rs[0] + i, 1, leta, lphi, 0, 0, 0, 0))
-                            continue;
-                        const float ptk = vp(Elem<KT>::f(T.template ld<KT>(J_PT, rs[0] + i)),
-                                             Elem<KT>::f(T.template ld<KT>(J_ETA, rs[0] + i)));
-                        if (!(ptk > P.jet_pt_min)) continue;
-                        ++ns;
-                        nbs += Elem<BT>::f(T.template ld<BT>(J_BTAG, rs[0] + i)) > P.btag_min ? 1 : 0;
-                    }
-                    if (ns >= 2 && nbs >= 1) pm |= 1ull << k;
+            if (JEC && active && nlep == 1) {
+                // corrected jets need no common order: each accepted jet's
+                // table position is found once, then the variations that
+                // select it form a mask; per variation the masks record one
+                // selected jet, two or more, and a selected b-jet
+                uint64_t one = 0, two = 0, bsel = 0;
+                for (int i = rs[0]; i < rt[0]; ++i) {
+                    if (!jet_acc<KT>(T, P, i, 1, leta, lphi, 0, 0, 0, 0)) continue;
+                    const float pt = Elem<KT>::f(T.template ld<KT>(J_PT, i));
+                    const JecPos jp = jec_pos(jt, pt, Elem<KT>::f(T.template ld<KT>(J_ETA, i)));
+                    uint64_t sel = 0;
+                    for (int k = 0; k < P.n_var; ++k)
+                        if (__fmul_rn(pt, jec_factor(jt, k, jp)) > P.jet_pt_min) sel |= 1ull << k;
+                    two |= one & sel;
+                    one |= sel;
+                    if (Elem<BT>::f(T.template ld<BT>(J_BTAG, i)) > P.btag_min) bsel |= sel;
                 }
+                pm = two & bsel;
             }
             const uint64_t qm = DEBUG ? (valid ? (P.n_var >= 64 ? ~0ull : ((1ull << P.n_var) - 1ull)) : 0ull) : pm;
             const bool q = qm != 0ull;
@@ -901,7 +935,7 @@ __global__ void __launch_bounds__(NT, 1)
                 for (uint64_t m = qm; m; m &= m - 1) {
                     const int k = __ffsll(static_cast<long long>(m)) - 1;
                     PairRes R;
-                    process_pair(J, VarPt{s_scales[k], k, use_jec, jt}, P, R);
+                    process_pair(J, VarPt<JEC>{s_scales[k], k, jt}, P, R);
                     if (nlep >= 1) {
                         R.v[13] = lpt;
                         R.v[14] = leta;
@@ -961,6 +995,7 @@ struct FusedArgs {
     hepacc_dtype offsets_type, btag_type;
     bool debug;
     bool flat;
+    bool jec;           // correction tables (built for blocks of kDebugBlock threads only)
     int block;          // threads per block (a built block size)
     int grid;           // 0 = as many resident blocks as fit (one per SM)
     bool cap_grid;      // no more blocks than tiles (plans keep the full grid to stay reusable)
@@ -1011,21 +1046,41 @@ hepacc_status launch_fused(K kernel, const FusedArgs& a) {
 
 template <typename KT, int NT>
 hepacc_status run_fused_nt(const FusedArgs& a) {
+    // the btag type of flat launches and of correction tables: F32 with F32
+    // kinematics, F16 with half kinematics
+    using HB = typename std::conditional<std::is_same<KT, float>::value, float, __half>::type;
+    if (a.jec) {
+        // correction tables: blocks of kDebugBlock threads only
+        if constexpr (NT == kDebugBlock) {
+            if (a.btag_type != (std::is_same<KT, float>::value ? HEPACC_F32 : HEPACC_F16))
+                return fail(HEPACC_ERR_DTYPE, "with correction tables btag must be F32 with F32 kinematics, F16 with half");
+            if (a.flat) {
+                if (a.offsets_type != HEPACC_I64) return fail(HEPACC_ERR_DTYPE, "batched launches need I64 offsets");
+                return launch_fused(k_fused<KT, HB, int64_t, false, true, NT, true>, a);
+            }
+            if (a.offsets_type == HEPACC_I32)
+                return a.debug ? launch_fused(k_fused<KT, HB, int32_t, true, false, NT, true>, a)
+                               : launch_fused(k_fused<KT, HB, int32_t, false, false, NT, true>, a);
+            return a.debug ? launch_fused(k_fused<KT, HB, int64_t, true, false, NT, true>, a)
+                           : launch_fused(k_fused<KT, HB, int64_t, false, false, NT, true>, a);
+        } else {
+            return fail(HEPACC_ERR_INVALID_ARG, "correction tables run in blocks of %d threads", kDebugBlock);
+        }
+    }
     if (a.flat) {
         // flat launches: int64 offsets, btag F32 with F32 kinematics, F16 with half
         if (a.offsets_type != HEPACC_I64) return fail(HEPACC_ERR_DTYPE, "batched launches need I64 offsets");
-        using BT = typename std::conditional<std::is_same<KT, float>::value, float, __half>::type;
-        return launch_fused(k_fused<KT, BT, int64_t, false, true, NT>, a);
+        return launch_fused(k_fused<KT, HB, int64_t, false, true, NT, false>, a);
     }
     auto go = [&](auto bt, auto ot) -> hepacc_status {
         using BT = typename decltype(bt)::type;
         using O = typename decltype(ot)::type;
         if constexpr (NT == kDebugBlock) {
-            if (a.debug) return launch_fused(k_fused<KT, BT, O, true, false, NT>, a);
+            if (a.debug) return launch_fused(k_fused<KT, BT, O, true, false, NT, false>, a);
         } else {
             if (a.debug) return fail(HEPACC_ERR_INVALID_ARG, "per-event outputs run in blocks of %d threads", kDebugBlock);
         }
-        return launch_fused(k_fused<KT, BT, O, false, false, NT>, a);
+        return launch_fused(k_fused<KT, BT, O, false, false, NT, false>, a);
     };
     auto with_o = [&](auto bt) -> hepacc_status {
         if (a.offsets_type == HEPACC_I32) return go(bt, chain::Tag<int32_t>{});

@@ -188,6 +188,15 @@ def test_chain_jet_energy_corrections(H, orc, fmt):
     print(fmt, check(H, orc, batch, shifts, jec=synth.jec_tables(shifts)))
 
 
+@pytest.mark.parametrize("lam_jet,n", [(4.0, 60_013), (60.0, 1_201)])
+def test_chain_jet_energy_corrections_histograms_only(H, orc, lam_jet, n):
+    # without per-event outputs only the pairs whose corrected jets pass are
+    # queued; events of more than 64 jets take the unbuffered path
+    batch = synth.generate(n, 29, lam_jet=lam_jet)
+    shifts = synth.variation_shifts(9)
+    print(lam_jet, check(H, orc, batch, shifts, per_event=False, jec=synth.jec_tables(shifts)))
+
+
 def test_chain_constant_corrections_equal_scales(H):
     # a table whose every entry is float32(1 + 0.01 k) is the scale variation k
     batch = synth.generate(30_007, 19)

@@ -132,3 +132,4 @@ def test_run_chain_debug_content_length(H):
     r = subprocess.run([sys.executable, "-c", CHILD_LEN], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
