@@ -231,18 +231,36 @@ def cpu_oracle_all_cores(batch, n_sample):
                       f"slowest shard {worst:.2f} s"}
 
 
+def headline_config(n_events, world):
+    """The headline workload's config (both arms)."""
+    return {"workload": WORKLOAD, "events_per_gpu": n_events, "offsets": "int64", "columns": "float32",
+            "variations": 1, "histograms": 20, "bins": 100, "l2": "inputs larger than L2 (no flush needed)",
+            "parallelism": f"dp{world} (independent event shards)"}
+
+
 def run_reference(args, rank, world):
+    """The oracle (the reference of this method) on the headline workload:
+    each step the next 300k-event window of the same 10M events, single
+    threaded on the host. Rank 0 only."""
     if rank != 0:
         return
     from paper_1906_06242_gb300 import synth
     per_step = 300_000
-    batch = synth.generate(per_step, 1)
+    batch = synth.generate(args.events, 1)
+    per_step = min(per_step, batch.n_events)
     from oracle import oracle
     oracle.build()
     times = []
     for i in range(args.warmup + args.steps):
+        a = (i * per_step) % max(1, batch.n_events - per_step + 1)
+        # events [a, a + per_step): offsets sliced, columns shared (event i
+        # owns [off[i], off[i+1]) of the full columns)
+        sub = synth.EventBatch(n_events=per_step, jet_offsets=batch.jet_offsets[a:a + per_step + 1],
+                               mu_offsets=batch.mu_offsets[a:a + per_step + 1],
+                               el_offsets=batch.el_offsets[a:a + per_step + 1], cols=batch.cols,
+                               weight=batch.weight[a:a + per_step])
         t0 = time.perf_counter()
-        oracle.run_chain(batch, synth.CUTS, synth.HIST_SPECS, [0], per_event=False)
+        oracle.run_chain(sub, synth.CUTS, synth.HIST_SPECS, [0], per_event=False)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     tot = sum(times)
@@ -250,9 +268,10 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "events_per_step_sample": per_step},
+            "data": "synthetic", "config": headline_config(batch.n_events, world),
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} events of the {WORKLOAD} generator per step"},
+                             "sample": f"per step the next {per_step}-event window of the {batch.n_events}-event "
+                                       f"{WORKLOAD} workload, 1 variation, single-threaded"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -522,10 +541,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_gpu": batch.n_events, "offsets": "int64",
-                   "columns": "float32", "variations": 1, "histograms": 20, "bins": 100,
-                   "l2": "inputs larger than L2 (no flush needed)", "input_bytes": int(alg_bytes),
-                   "parallelism": f"dp{world} (independent event shards)"},
+        "config": headline_config(batch.n_events, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": f"{peak_kind} hbm_gbs",
                      "traffic": traffic, "traffic_from": counters.get("plain_f32", {}).get("capture"),
