@@ -226,9 +226,12 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
                   int flat_samples, int blocks_per_sm, fused::FLayout& L) {
     std::memset(&L, 0, sizeof L);
     if (S < 2 || S > fused::kMaxStages) return false;
+    // a tile's objects of a collection: mean m = NT lambda, Poisson spread
+    // sqrt(m); the stage holds m + 3 sqrt(m) + 16 (a tile beyond it, about
+    // one in a thousand, is read from global memory)
     auto cap_of = [&](double lam) {
         const double m = NT * lam;
-        return static_cast<uint32_t>(((static_cast<size_t>(m + 4.0 * std::sqrt(m) + 64.0)) + 31) & ~size_t(31));
+        return static_cast<uint32_t>(((static_cast<size_t>(m + 3.0 * std::sqrt(m) + 16.0)) + 31) & ~size_t(31));
     };
     const uint32_t cj = cap_of(lam_j), cm = cap_of(lam_m), ce = cap_of(lam_e);
     uint32_t off = 0;
@@ -282,8 +285,12 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
     // per buffered jet: 7 floats and the acceptance byte, with correction
     // tables also its table position (int32 offset, float weight)
     const size_t per_ev = 11 * 4 + 2 * 8, per_j = 7 * 4 + 1 + (jec ? 8 : 0);
-    int cap_ev = std::min(2 * NT, 65535);
-    if (static_cast<size_t>(cap_ev) * per_ev + 4 * 32 * per_j > avail) cap_ev = NT;
+    // events and jets in the proportion a passing event brings (its summary
+    // and lambda_j jets, plus one), so that neither side fills first;
+    // between 32 and 2 NT events
+    const double per_pass = static_cast<double>(per_ev) + (lam_j + 1.0) * static_cast<double>(per_j);
+    int cap_ev = static_cast<int>(std::min<double>(2.0 * NT, static_cast<double>(avail) / per_pass)) & ~31;
+    cap_ev = std::max(cap_ev, 32);
     if (static_cast<size_t>(cap_ev) * per_ev + 4 * 32 * per_j > avail) return false;
     const int cap_j = static_cast<int>(std::min<size_t>((avail - cap_ev * per_ev) / per_j, 65535));
     L.cap_ev = cap_ev;
@@ -319,18 +326,21 @@ bool fused_layout(int NT, int S, double lam_j, double lam_m, double lam_e, size_
 }
 
 // The configuration of single-sample launches (hepacc_run_chain): blocks of
-// kDebugBlock threads laid out for two blocks per SM with two stages (the
-// rest of the shared memory goes to the pair buffer; measured fastest on
-// GB300 for the 10M-event FP32 set: 2.56 ms against 3.16 ms with three
-// stages and 3.30 ms for one block of 256 per SM); one block per SM if that
-// does not fit.
+// kDebugBlock threads with two stages, laid out for the most blocks per SM
+// (three, then two) whose pair buffer holds at least half a tile's jets
+// (smaller buffers drain so often that the extra warps do not pay: as plan
+// candidates on GB300, 10M-event FP32 set, a 305-jet buffer at three
+// blocks per SM ran 4.3 ms against 2.7 ms at two); else one block per SM.
 bool single_config(double lam_j, double lam_m, double lam_e, size_t kes, size_t bes, const ChainParams& P,
                    fused::FLayout& L, int& NT) {
     NT = fused::kDebugBlock;
     // objects per event so dense that no stage fits: smaller stages (the
     // tiles that do not fit one are read from global memory)
     for (double f = 1.0; f >= 1.0 / 64; f *= 0.5) {
-        if (fused_layout(NT, 2, lam_j * f, lam_m * f, lam_e * f, kes, bes, P, 0, 2, L)) return true;
+        for (int bps = fused::min_blocks_for(NT); bps >= 2; --bps)
+            if (fused_layout(NT, 2, lam_j * f, lam_m * f, lam_e * f, kes, bes, P, 0, bps, L) &&
+                L.cap_j >= 0.5 * NT * lam_j)
+                return true;
         if (fused_layout(NT, 2, lam_j * f, lam_m * f, lam_e * f, kes, bes, P, 0, 1, L)) return true;
     }
     return fused_layout(NT, 2, 1.0, 0.25, 0.25, kes, bes, P, 0, 1, L);
@@ -698,11 +708,14 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
             // each block is laid out for) x stages
             // (correction tables: blocks of kDebugBlock threads only)
             for (int nt : fused::kBlocks)
-                for (int bps = 1; bps * nt <= 256 && (!p->P.jec_contents || nt == fused::kDebugBlock); ++bps)
+                for (int bps = 1; bps <= fused::min_blocks_for(nt) && (!p->P.jec_contents || nt == fused::kDebugBlock);
+                     ++bps)
                     for (int S = 2; S <= fused::kMaxStages; ++S) {
                         Candidate c{};
+                        // (a buffer for a quarter of a tile's jets: only passing
+                        // events append theirs)
                         if (fused_layout(nt, S, lam_j, lam_m, lam_e, kes, bes, p->P, flat_samples, bps, c.FL) &&
-                            c.FL.cap_j >= nt * lam_j) {
+                            c.FL.cap_j >= nt * lam_j / 4) {
                             c.compacting = true;
                             c.hmode = H_GLOBAL;
                             c.cluster = 1;

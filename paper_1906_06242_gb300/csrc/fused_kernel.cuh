@@ -440,8 +440,13 @@ __device__ __forceinline__ void emit(const ChainParams& P, const float* s_edges,
     }
 }
 
+// Blocks per SM the register allocation is sized for: 128-thread blocks at
+// three per SM (168 registers, the pair work without spills), the others as
+// many as their shared-memory layouts allow (64: four, 256: one).
+constexpr int min_blocks_for(int nt) { return nt == 128 ? 3 : nt == 64 ? 4 : 1; }
+
 template <typename KT, typename BT, typename OffT, bool DEBUG, bool FLAT, int NT, bool JEC>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, min_blocks_for(NT))
     k_fused(const __grid_constant__ FLayout L, const __grid_constant__ ChainParams P,
             const __grid_constant__ BatchDesc B) {
     static_assert(NT % 32 == 0 && NT <= 1024, "block of whole warps");

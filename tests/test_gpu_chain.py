@@ -207,5 +207,11 @@ def test_chain_constant_corrections_equal_scales(H):
     b = run_gpu(H, batch, shifts)
     for key in ("pass", "njet", "nb", "idx", "counts"):
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
-    np.testing.assert_array_equal(a["vars"], b["vars"])
+    # the two are separate kernel builds: the variables computed in a fixed
+    # order of binary32 operations agree bit for bit, the masses and |sum pT|
+    # (whose products the compiler may fuse differently) to the mass tolerance
+    loose = list(CC.MASS_VARS) + [CC.PTJJJ]
+    exact = [h for h in range(synth.N_HIST) if h not in loose]
+    np.testing.assert_array_equal(a["vars"][:, exact], b["vars"][:, exact])
+    np.testing.assert_allclose(a["vars"][:, loose], b["vars"][:, loose], rtol=CC.REL_MASS, atol=0)
     assert H.device_error() == 0
