@@ -427,12 +427,19 @@ typedef struct hepacc_plan hepacc_plan;
  * offsets and the same kin_type and btag_type (F32 with F32, F16 with F16
  * or BF16). Histogram placement is a kernel configuration: block-private
  * shared memory, shared memory spread over a cluster of 8 or 16 blocks
- * (updated through distributed shared memory), or global memory. Without
- * HEPACC_PLAN_AUTOTUNE the first candidate placement (HEPACC_PLAN_HIST_*)
- * that fits, in that order, is taken; with it,
- * every candidate is run three times on the samples (DEVICE pointers given
+ * (updated through distributed shared memory), or global memory. The
+ * candidates: the kernel of hepacc_run_chain with blocks of 64, 128 and
+ * 256 threads x blocks per SM x 2-4 stages (every layout that fits), then
+ * the walking kernel with each allowed shared-memory placement. Without
+ * HEPACC_PLAN_AUTOTUNE the first candidate is taken; with it, every
+ * candidate is run three times on the samples (DEVICE pointers given
  * here must be valid), the fastest kept, and the outputs cleared to zero
- * afterwards, on `stream`, which the call synchronises. config is HOST
+ * afterwards, on `stream`, which the call synchronises. The choice is
+ * remembered for the life of the process, keyed by the GPU's name, the
+ * configuration's values, the column types, the allowed placements, the
+ * samples per launch, the objects per event (to 0.1) and the events (to a
+ * power of two); a later plan with the same key takes it without timing
+ * (hepacc_plan_describe then reports "tuned_from_cache": true). config is HOST
  * memory and copied; the sample and output structs are copied; the device
  * buffers they point to must stay valid while runs use them. With
  * HEPACC_PLAN_VALIDATE (or HEPACC_DEBUG set, as for hepacc_run_chain) every

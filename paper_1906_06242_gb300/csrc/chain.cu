@@ -5,6 +5,10 @@
 // layouts and histogram placements, replayed as a CUDA graph, reusable over
 // new batches of the same shape).
 #include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -441,6 +445,7 @@ struct hepacc_plan {
     hepacc_dtype kin, btag;
     Candidate c;         // the chosen configuration
     float tuned_ms;
+    bool tuned_from_cache;   // the choice came from the autotune cache
     int n_candidates;
     std::vector<std::string> tried;   // candidate descriptions and times (JSON fragments)
     cudaGraph_t graph;
@@ -534,6 +539,47 @@ std::string describe(const Candidate& c) {
         snprintf(buf, sizeof buf, "{\"kernel\": \"walking\", \"histograms\": \"%s\", \"cluster\": %d, \"block\": %d",
                  c.hmode == H_SMEM ? "block" : "cluster", c.cluster, c.block);
     return buf;
+}
+
+// The autotune cache of this process: the configuration an earlier plan of
+// the same shape chose, keyed by the GPU's name, the configuration's
+// values (cuts, edges, scales, tables: a hash), the column types, the
+// allowed placements, the launch's sample count, the objects per event
+// (to 0.1) and the events (to a power of two).
+struct TuneChoice {
+    bool compacting;
+    int hmode, cluster, block, blocks_per_sm, stages;
+    float ms;
+};
+std::mutex& tune_mu() {
+    static std::mutex m;
+    return m;
+}
+std::map<std::string, TuneChoice>& tune_cache() {
+    static std::map<std::string, TuneChoice> c;
+    return c;
+}
+std::string tune_key(const ChainParams& P, hepacc_dtype kin, hepacc_dtype btag, uint32_t allowed, int flat_samples,
+                     double lam_j, double lam_m, double lam_e, double events) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof prop);
+    cudaGetDeviceProperties(&prop, dev);
+    // FNV-1a over the configuration's bytes (ChainParams is zeroed before it
+    // is filled, so its padding hashes the same every time)
+    uint64_t h = 1469598103934665603ull;
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&P);
+    for (size_t i = 0; i < sizeof P; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|%016llx|%d|%d|%u|%d|%ld|%ld|%ld|%d", prop.name, static_cast<unsigned long long>(h),
+             static_cast<int>(kin), static_cast<int>(btag), allowed, flat_samples, std::lround(lam_j * 10),
+             std::lround(lam_m * 10), std::lround(lam_e * 10), events > 1 ? static_cast<int>(std::log2(events)) : 0);
+    return buf;
+}
+bool same_choice(const Candidate& c, const TuneChoice& t) {
+    return c.compacting == t.compacting && c.hmode == t.hmode && c.cluster == t.cluster && c.block == t.block &&
+           c.blocks_per_sm == t.blocks_per_sm && c.stages == t.stages;
 }
 
 // Times every candidate (one warm-up run, two timed) on the plan's samples
@@ -752,10 +798,30 @@ hepacc_status hepacc_plan_create(const hepacc_chain_config* cfg, int32_t n_sampl
     p->tuned_ms = -1.0f;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int pick = 0;
+    p->tuned_from_cache = false;
+    const std::string key = tune_key(p->P, p->kin, p->btag, allowed, flat_samples, lam_j0, lam_m0, lam_e0, events);
     if (flags & HEPACC_PLAN_AUTOTUNE) {
+        std::lock_guard<std::mutex> g(tune_mu());
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end())
+            for (size_t i = 0; i < cands.size(); ++i)
+                if (same_choice(cands[i], it->second)) {
+                    pick = static_cast<int>(i);
+                    p->tuned_ms = it->second.ms;
+                    p->tuned_from_cache = true;
+                    break;
+                }
+    }
+    if ((flags & HEPACC_PLAN_AUTOTUNE) && !p->tuned_from_cache) {
         pick = autotune(p, cands, s, p->tuned_ms);
         cudaGetLastError();   // failures of rejected candidates
         if (pick < 0) return drop(fail(HEPACC_ERR_CUDA, "no candidate chain configuration ran"));
+        {
+            const Candidate& c = cands[pick];
+            std::lock_guard<std::mutex> g(tune_mu());
+            tune_cache()[key] =
+                TuneChoice{c.compacting, c.hmode, c.cluster, c.block, c.blocks_per_sm, c.stages, p->tuned_ms};
+        }
         st = zero_outputs(p, s);
         if (st == HEPACC_OK) {
             const cudaError_t e = cudaStreamSynchronize(s);
@@ -821,9 +887,9 @@ hepacc_status hepacc_plan_describe(const hepacc_plan* p, char* buf, int32_t len)
     const unsigned smem = p->c.compacting ? p->c.FL.total : p->c.L.total;
     snprintf(buf, static_cast<size_t>(len),
              "{\"chosen\": %s, \"smem_bytes\": %u}, \"launches\": %zu, \"graph\": %s, \"candidates\": %d, "
-             "\"tuned_ms\": %.4f, \"tried\": [%s]}",
+             "\"tuned_ms\": %.4f, \"tuned_from_cache\": %s, \"tried\": [%s]}",
              describe(p->c).c_str(), smem, nl, p->exec ? "true" : "false", p->n_candidates,
-             static_cast<double>(p->tuned_ms), tried.c_str());
+             static_cast<double>(p->tuned_ms), p->tuned_from_cache ? "true" : "false", tried.c_str());
     return HEPACC_OK;
 }
 

@@ -192,3 +192,31 @@ def test_plan_with_jet_energy_corrections(H, orc):
         ref = orc.run_chain(s, synth.CUTS, synth.HIST_SPECS, shifts, jec=jec)
         CC.compare_hists(o.counts.cpu().numpy().view(np.uint64), o.sumw.cpu().numpy(), o.sumw2.cpu().numpy(), ref,
                          s.weight, ref["nbins"], ref["edges"])
+
+
+def test_plan_autotune_cache(H, orc):
+    # a second autotuned plan of the same shape takes the first one's choice
+    # without timing; another configuration is tuned afresh
+    samples = [synth.generate(n, 700 + i, offset_dtype=np.int64) for i, n in enumerate([30_011, 8_009])]
+    shifts = synth.variation_shifts(3)
+    cfg = config(H, shifts)
+    dbs = [H.DeviceBatch.from_host(s) for s in samples]
+    flags = H.PLAN_AUTOTUNE | H.PLAN_HIST_GLOBAL
+    outs_a = [H.ChainOutputs(cfg, s.n_events) for s in samples]
+    a = H.hepacc_plan_create(cfg, dbs, outs_a, flags=flags)
+    da = a.describe()
+    outs_b = [H.ChainOutputs(cfg, s.n_events) for s in samples]
+    b = H.hepacc_plan_create(cfg, dbs, outs_b, flags=flags)
+    db_ = b.describe()
+    assert db_["tuned_from_cache"] and db_["tried"] == []
+    assert db_["chosen"] == da["chosen"]
+    b.run()
+    torch.cuda.synchronize()
+    cfg2 = config(H, synth.variation_shifts(5))
+    c = H.hepacc_plan_create(cfg2, dbs, [H.ChainOutputs(cfg2, s.n_events) for s in samples], flags=flags)
+    assert not c.describe()["tuned_from_cache"]
+    for p in (a, b, c):
+        p.close()
+    assert H.device_error() == 0
+    res = [(o.counts.cpu().numpy().view(np.uint64), o.sumw.cpu().numpy(), o.sumw2.cpu().numpy()) for o in outs_b]
+    check_samples(orc, samples, shifts, res)
