@@ -30,6 +30,20 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "plain_10m"
 METRIC = "events/s and HBM GB/s (% of peak) for the full chain, plain vs BF16+batched, 1 GB300"
 N_EVENTS = 10_000_000
+
+# The paper's own rates (Sections III and IV), other hardware and other
+# workloads: context for the figures, not a baseline of this workload.
+PAPER_CONTEXT = {
+    "hardware": "Numba kernels; CPU Xeon E5-2687W v4 @ 3.00 GHz, GPU GeForce Titan X",
+    "kernels_events_per_s": {"value": 1e7, "note": "order of magnitude (tens of MHz) per kernel, ~11M preloaded "
+                                                     "events, GPU ~20-30x one CPU thread"},
+    "delta_r_mask_events_per_s": {"cpu_1_thread": 7e6, "gpu": 7e6 * 14},
+    "full_analysis_events_per_s": {"partial_systematics": {"cpu_1_thread": 50e3, "cpu_4_threads": 119e3,
+                                                           "gpu": 440e3},
+                                   "full_systematics": {"cpu_1_thread": 1.4e3, "cpu_4_threads": 4.0e3,
+                                                        "gpu": 20e3},
+                                   "note": "CMS Open Data analysis with a DNN and ~1000 histograms"},
+}
 N_VARIATIONS_BATCHED = 21
 
 
@@ -554,6 +568,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "paper_context": PAPER_CONTEXT,
     }
     if extra:
         line["forms"] = extra
