@@ -21,6 +21,8 @@ def test_reference_arm_json_line():
     assert d["unit"] == "events/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1 and d["ms_per_step"] > 0
     assert d["config"]["workload"] and d["data"] == "synthetic"
+    # the same config as the GPU arm's line (the headline workload)
+    assert d["config"] == bench.headline_config(bench.N_EVENTS, 1)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
