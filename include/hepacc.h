@@ -375,7 +375,8 @@ typedef struct {
  *  1. leptons (muons and electrons) selected by pt > lep_pt_min,
  *     |eta| < lep_abseta_max, tight != 0, iso < lep_iso_max; n_lep counts
  *     both; "the lepton" is the first selected muon, else electron;
- *  2. jets: pt_k = pt * s_k (binary32); selected if pt_k > jet_pt_min,
+ *  2. jets: pt_k = pt * s_k (binary32; with correction tables pt * the
+ *     variation's table factor, see hepacc_chain_config); selected if pt_k > jet_pt_min,
  *     |eta| < jet_abseta_max and Delta R^2 >= dr2_cut (as in
  *     hepacc_mask_deltar) to every selected lepton;
  *  3. n_jet, n_b (btag > btag_min); pass = n_lep == 1, n_jet >= 2, n_b >= 1;
@@ -392,8 +393,9 @@ typedef struct {
  * non-decreasing, offsets[n_events] <= the collection's content length; the
  * call waits for the check); a failure returns HEPACC_ERR_DEVICE_CHECK
  * before the chain is launched.
- * Shared memory: the call uses up to the device's per-block opt-in limit
- * (one resident block per SM). */
+ * Shared memory: the call lays out blocks of 128 threads for three, two or
+ * one resident block per SM (the most whose pair buffer holds half a
+ * tile's jets), using up to the device's per-block opt-in limit. */
 hepacc_status hepacc_run_chain(const hepacc_event_batch *batch, const hepacc_chain_config *config,
                                const hepacc_chain_outputs *out, hepacc_stream stream);
 
