@@ -842,6 +842,22 @@ def test_get_bin_contents_interpolation(orc):
     np.testing.assert_array_equal(one, [6, 6, 6])
 
 
+def test_get_bin_contents_interpolation_matches_numpy_interp(orc):
+    # uneven (log-spaced, as the correction tables' pt bins) edges: linear
+    # interpolation between bin centres, clamped at the first and last
+    # centre, is numpy.interp over the centres (binary64 there, binary32 in
+    # the oracle: equal to a few ulp of the contents)
+    rng = np.random.default_rng(53)
+    edges = np.geomspace(20.0, 1000.0, 25).astype(np.float32)
+    centres = ((edges[:-1] + edges[1:]) * np.float32(0.5)).astype(np.float32)
+    y = rng.uniform(0.8, 1.2, size=24).astype(np.float32)
+    contents = np.concatenate([[7.0], y, [-7.0]]).astype(np.float32)
+    v = np.concatenate([rng.uniform(5.0, 1500.0, 20000), centres, edges]).astype(np.float32)
+    out = orc.get_bin_contents(v, edges, contents, interpolate=True)
+    want = np.interp(v.astype(np.float64), centres.astype(np.float64), y.astype(np.float64))
+    np.testing.assert_allclose(out, want, rtol=0, atol=4e-7 * 1.2)
+
+
 # ---------------------------------------------------------------------------
 # jet-pt scale variation: one binary32 product, round to nearest even
 # ---------------------------------------------------------------------------
